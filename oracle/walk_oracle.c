@@ -1,0 +1,480 @@
+/*
+ * FP64 CPU oracle for the mixture-of-media random walk.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file; only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark do.  It shares no code, header, table or constant
+ * generator with the CUDA path.
+ *
+ * What it computes (paper, Sec. 4.1):
+ *   - the BSSRDF as a path integral over paths whose contribution is the
+ *     product of boundary terms, transmittances T and albedo-scaled phase
+ *     functions alpha*sigma_t*pf (the display defining f_SSS after Eq. 2);
+ *   - its radial form under normal incidence, R_d(r) = R * P_d(r) (Eq. 3);
+ *   - the K-media mixture S = sum_k w_k S_k with sum_k w_k = 1 (Eq. 4),
+ *     estimated by picking ONE medium per path, with probability w_k, before
+ *     the walk starts (Sec. 4.1 last paragraph, Sec. 6 "each photon randomly
+ *     selects a medium", Sec. 7 "select the medium ... adjust the pdf").
+ *
+ * The estimator is the textbook analog / weighted random walk, written step
+ * by step in double precision:
+ *   select medium -> enter (weight 1-R0) -> loop { exponential flight with
+ *   sigma_t; if the flight reaches a face, smooth-dielectric Fresnel
+ *   reflect-or-exit; otherwise a collision: albedo weighting with Russian
+ *   roulette (or analog absorption), Henyey-Greenstein scattering with g }
+ *   -> tally the exit weight into R, the radial histogram, R_k, R1, T.
+ *
+ * Random numbers: both this oracle and the CUDA path implement ONE
+ * counter-based generator, Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11), from its published
+ * definition, with the same counter layout:
+ *     key     = (seed_lo, seed_hi)
+ *     counter = (step, path, instance, tag)   tag 0 = walk step, 1 = selection
+ * and the same 24-bit uniform u = ((x >> 8) + 0.5) * 2^-24 in (0,1).
+ * Everything else (flights, Fresnel, HG, rotation, weights, tallies) is
+ * double precision here, so GPU-vs-oracle differences come only from the
+ * kernel's binary32 rounding.  The one integer decision that floating point
+ * takes before any other (which medium a path uses) is taken in binary32,
+ * the kernel's precision, on both sides.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_KMAX 4
+#define ORC_NBINS_MAX 4096
+#define ORC_NV_MAX (ORC_NBINS_MAX + 1 + ORC_KMAX + 5)
+#define ORC_CHUNK 1024
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (SC'11): 10 rounds of the 4x32 S-box with a Weyl key bump. */
+/* ------------------------------------------------------------------------ */
+static const uint32_t PHILOX_M0 = 0xD2511F53u; /* round multipliers */
+static const uint32_t PHILOX_M1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_W0 = 0x9E3779B9u; /* key schedule (golden ratio) */
+static const uint32_t PHILOX_W1 = 0xBB67AE85u; /* key schedule (sqrt(3)-1) */
+
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                          uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += PHILOX_W0;
+    k1 += PHILOX_W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 24-bit uniform strictly inside (0,1): never 0 (so -ln u is finite), never 1. */
+static double u24(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+static void draw4(uint64_t seed, uint32_t step, uint32_t path, uint32_t inst,
+                  uint32_t tag, double u[4]) {
+  uint32_t ctr[4] = {step, path, inst, tag};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t x[4];
+  oracle_philox4x32_10(ctr, key, x);
+  for (int i = 0; i < 4; ++i) u[i] = u24(x[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Physics helpers (exported so the tests can check them one by one).        */
+/* ------------------------------------------------------------------------ */
+
+/* Unpolarised Fresnel reflectance of a smooth dielectric interface, light
+ * going from the medium (index n) to the outside (index 1), incidence cosine
+ * cos_i.  Total internal reflection when n*sin_i >= 1.  (Sec. 8: smooth
+ * Fresnel boundary.) */
+double oracle_fresnel(double cos_i, double n) {
+  if (n == 1.0) return 0.0;
+  if (cos_i > 1.0) cos_i = 1.0;
+  double sin_i = sqrt(fmax(0.0, 1.0 - cos_i * cos_i));
+  double sin_t = n * sin_i;
+  if (sin_t >= 1.0) return 1.0;
+  double cos_t = sqrt(1.0 - sin_t * sin_t);
+  double rs = (n * cos_i - cos_t) / (n * cos_i + cos_t);
+  double rp = (cos_i - n * cos_t) / (cos_i + n * cos_t);
+  return 0.5 * (rs * rs + rp * rp);
+}
+
+/* Henyey-Greenstein cosine by inversion of its CDF; isotropic for |g|<1e-4. */
+double oracle_hg_mu(double g, double u) {
+  double mu;
+  if (fabs(g) < 1e-4) {
+    mu = 2.0 * u - 1.0;
+  } else {
+    double t = (1.0 - g * g) / (1.0 - g + 2.0 * g * u);
+    mu = (1.0 + g * g - t * t) / (2.0 * g);
+  }
+  if (mu > 1.0) mu = 1.0;
+  if (mu < -1.0) mu = -1.0;
+  return mu;
+}
+
+/* d/dg log p_HG(mu; g), p_HG(mu) = (1-g^2) / (2 (1+g^2-2 g mu)^{3/2}). */
+double oracle_hg_dlogp_dg(double g, double mu) {
+  return -2.0 * g / (1.0 - g * g) - 3.0 * (g - mu) / (1.0 + g * g - 2.0 * g * mu);
+}
+
+/* Rotate direction u by polar cosine mu and azimuth phi (spherical frame
+ * about the current direction; special case when u is nearly along z). */
+void oracle_rotate(double u[3], double mu, double phi) {
+  double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+  double cp = cos(phi), sp = sin(phi);
+  double ux = u[0], uy = u[1], uz = u[2];
+  double nx, ny, nz;
+  if (fabs(uz) > 1.0 - 1e-6) {
+    nx = st * cp;
+    ny = st * sp;
+    nz = (uz >= 0.0 ? 1.0 : -1.0) * mu;
+  } else {
+    double tmp = sqrt(1.0 - uz * uz);
+    nx = st * (ux * uz * cp - uy * sp) / tmp + ux * mu;
+    ny = st * (uy * uz * cp + ux * sp) / tmp + uy * mu;
+    nz = -st * cp * tmp + uz * mu;
+  }
+  double nrm = sqrt(nx * nx + ny * ny + nz * nz);
+  u[0] = nx / nrm; u[1] = ny / nrm; u[2] = nz / nrm;
+}
+
+/* Medium choice with probability w_k / sum(w): the first k whose running
+ * CDF exceeds u, the last medium taking any round-off remainder.  Taken in
+ * binary32 (the kernel's precision) so both sides make the same choice. */
+int oracle_select_medium(const float* w, int K, double u) {
+  float total = 0.0f;
+  for (int k = 0; k < K; ++k) total += w[k];
+  float inv = 1.0f / total;
+  float us = (float)u;
+  float cdf = 0.0f;
+  for (int k = 0; k < K - 1; ++k) {
+    cdf += w[k] * inv;
+    if (us < cdf) return k;
+  }
+  return K - 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One path.                                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int nbins;
+  double r_max_mm;
+  int mode;            /* 0 = albedo weighting + Russian roulette, 1 = analog */
+  double rr_threshold; /* W_th; 0 disables roulette (weight mode only) */
+  int entry_fresnel;   /* 1: entry weight 1-R0 (specular excluded) */
+  uint32_t max_steps;
+  uint64_t seed;
+} oracle_opts;
+
+typedef struct {
+  int exit_kind;    /* 0 top, 1 bottom, 2 absorbed/roulette, 3 truncated */
+  int medium;
+  int bin;          /* top exits: bin index, nbins = overflow */
+  double weight;    /* exit weight (0 unless exit_kind is 0 or 1) */
+  double absorbed;  /* weight deposited by collisions */
+  uint32_t steps;   /* random-number draws used by the loop */
+  uint32_t n_coll;  /* collisions (scattering or absorption events) */
+  double length;    /* total distance travelled inside the medium, mm */
+  double dlogp_dg;  /* sum over scatterings of d log p_HG / dg */
+  double x, y;      /* exit point on the face */
+} oracle_path;
+
+void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
+                       const float* w, int K, int64_t n_inst, int64_t inst,
+                       uint32_t path, double thickness_mm, double n_rel,
+                       const oracle_opts* o, oracle_path* res) {
+  double u[4];
+  memset(res, 0, sizeof(*res));
+  /* Medium selection once per path, before the walk (Eq. 4, Sec. 7). */
+  float wk[ORC_KMAX];
+  for (int k = 0; k < K; ++k) wk[k] = w[(int64_t)k * n_inst + inst];
+  draw4(o->seed, 0u, path, (uint32_t)inst, 1u, u);
+  int k = oracle_select_medium(wk, K, u[0]);
+  res->medium = k;
+  double a = alpha[(int64_t)k * n_inst + inst];
+  double st = sigma_t[(int64_t)k * n_inst + inst];
+  double gg = g[(int64_t)k * n_inst + inst];
+
+  /* Normal incidence at the origin (Eq. 3); weight after the entry BTDF. */
+  double R0 = (n_rel - 1.0) / (n_rel + 1.0);
+  R0 *= R0;
+  double W = o->entry_fresnel ? 1.0 - R0 : 1.0;
+  double pos[3] = {0.0, 0.0, 0.0};
+  double dir[3] = {0.0, 0.0, 1.0};
+  double d = thickness_mm; /* +inf: semi-infinite */
+
+  uint32_t step = 0;
+  for (;;) {
+    if (step >= o->max_steps) { res->exit_kind = 3; break; }
+    draw4(o->seed, step, path, (uint32_t)inst, 0u, u);
+    step++;
+    double s = -log(u[0]) / st; /* exponential free flight (transmittance T) */
+    double db = INFINITY;
+    if (dir[2] < 0.0) db = -pos[2] / dir[2];
+    else if (dir[2] > 0.0) db = (d - pos[2]) / dir[2];
+    if (db <= s) {
+      /* Reaches a face: move there, then smooth-dielectric Fresnel. */
+      pos[0] += db * dir[0];
+      pos[1] += db * dir[1];
+      int top = dir[2] < 0.0;
+      pos[2] = top ? 0.0 : d;
+      res->length += db;
+      double F = oracle_fresnel(fabs(dir[2]), n_rel);
+      if (u[1] < F) { dir[2] = -dir[2]; continue; }
+      res->exit_kind = top ? 0 : 1;
+      res->weight = W;
+      res->x = pos[0];
+      res->y = pos[1];
+      if (top) {
+        double r = sqrt(pos[0] * pos[0] + pos[1] * pos[1]);
+        double fb = floor(r * (double)o->nbins / o->r_max_mm);
+        res->bin = fb >= (double)o->nbins ? o->nbins : (int)fb;
+      }
+      break;
+    }
+    /* Collision inside the medium. */
+    for (int i = 0; i < 3; ++i) pos[i] += s * dir[i];
+    res->length += s;
+    res->n_coll++;
+    if (o->mode == 0) {
+      res->absorbed += W * (1.0 - a);
+      W *= a;
+      if (W < o->rr_threshold) {
+        if (u[3] < W / o->rr_threshold) W = o->rr_threshold;
+        else { res->exit_kind = 2; break; }
+      }
+    } else {
+      if (u[3] >= a) { res->absorbed += W; res->exit_kind = 2; break; }
+    }
+    double mu = oracle_hg_mu(gg, u[1]);
+    res->dlogp_dg += oracle_hg_dlogp_dg(gg, mu);
+    oracle_rotate(dir, mu, 2.0 * M_PI * u[2]);
+  }
+  res->steps = step;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Batched forward tallies.                                                   */
+/* ------------------------------------------------------------------------ */
+/* Outputs, all per instance, NULL allowed for any of them:
+ *   R, T, A, overflow, R1, truncated : [n_inst]
+ *   bins : [n_inst][nbins]      R_k : [n_inst][K]
+ *   se_R, se_T, se_A, se_R1 : [n_inst]   se_bins : [n_inst][nbins]
+ *   se_R_k : [n_inst][K]
+ * Each tally is the mean over the instance's N paths of the per-path
+ * contribution (a fraction of the incident power); se_* is the sample
+ * standard error of that mean. */
+typedef struct {
+  double *R, *T, *A, *bins, *overflow, *R_k, *R1, *truncated;
+  double *se_R, *se_T, *se_A, *se_bins, *se_R_k, *se_R1;
+  double *steps; /* mean random-number draws per path */
+} oracle_out;
+
+static double se_of(double s, double s2, double n) {
+  if (n < 2.0) return 0.0;
+  double m = s / n;
+  double v = (s2 / n - m * m) * n / (n - 1.0);
+  return v > 0.0 ? sqrt(v / n) : 0.0;
+}
+
+int oracle_walk(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
+                const float* g, const float* w, const uint32_t* n_paths,
+                const float* thickness_mm, double n_rel, const oracle_opts* o,
+                uint32_t path_offset, oracle_out* out) {
+  if (K < 1 || K > ORC_KMAX || o->nbins < 1 || o->nbins > ORC_NBINS_MAX) return 1;
+  const int nb = o->nbins;
+  /* per-path vector: [bins nb][overflow][R_k K][R1][T][A][trunc][steps] */
+  const int nv = nb + 1 + K + 5;
+  for (int64_t i = 0; i < n_inst; ++i) {
+    const uint32_t N = n_paths[i];
+    const double d = thickness_mm ? (double)thickness_mm[i] : INFINITY;
+    /* Fixed chunks of paths, each summed in path order, then the chunks in
+     * chunk order: the result does not depend on the thread count. */
+    const int64_t nch = ((int64_t)N + ORC_CHUNK - 1) / ORC_CHUNK;
+    double* ps = calloc((size_t)(nch > 0 ? nch : 1) * 2 * (size_t)nv, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      double* ls = ps + (size_t)ch * 2 * (size_t)nv;
+      double* ls2 = ls + nv;
+      double c[ORC_NV_MAX];
+      const int64_t p1 = (ch + 1) * ORC_CHUNK < (int64_t)N ? (ch + 1) * ORC_CHUNK : (int64_t)N;
+      for (int64_t p = ch * ORC_CHUNK; p < p1; ++p) {
+        oracle_path r;
+        oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i,
+                          path_offset + (uint32_t)p, d, n_rel, o, &r);
+        memset(c, 0, sizeof(double) * (size_t)nv);
+        if (r.exit_kind == 0) {
+          c[r.bin] = r.weight; /* bin or overflow slot */
+          c[nb + 1 + r.medium] = r.weight;
+          if (r.n_coll == 1) c[nb + 1 + K] = r.weight;
+        } else if (r.exit_kind == 1) {
+          c[nb + 1 + K + 1] = r.weight;
+        } else if (r.exit_kind == 3) {
+          c[nb + 1 + K + 3] = 1.0;
+        }
+        c[nb + 1 + K + 2] = r.absorbed;
+        c[nb + 1 + K + 4] = (double)r.steps;
+        for (int j = 0; j < nv; ++j) { ls[j] += c[j]; ls2[j] += c[j] * c[j]; }
+      }
+    }
+    double* s = calloc((size_t)nv, sizeof(double));
+    double* s2 = calloc((size_t)nv, sizeof(double));
+    for (int64_t ch = 0; ch < nch; ++ch)
+      for (int j = 0; j < nv; ++j) {
+        s[j] += ps[(size_t)ch * 2 * (size_t)nv + (size_t)j];
+        s2[j] += ps[(size_t)ch * 2 * (size_t)nv + (size_t)nv + (size_t)j];
+      }
+    free(ps);
+    const double n = (double)N;
+    double sR = 0.0, s2R = 0.0;
+    for (int b = 0; b <= nb; ++b) { sR += s[b]; s2R += s2[b]; }
+    /* a path exits through at most one slot, so sum of squares adds up */
+    if (out->R) out->R[i] = sR / n;
+    if (out->se_R) out->se_R[i] = se_of(sR, s2R, n);
+    for (int b = 0; b < nb; ++b) {
+      if (out->bins) out->bins[i * nb + b] = s[b] / n;
+      if (out->se_bins) out->se_bins[i * nb + b] = se_of(s[b], s2[b], n);
+    }
+    if (out->overflow) out->overflow[i] = s[nb] / n;
+    for (int k = 0; k < K; ++k) {
+      if (out->R_k) out->R_k[i * K + k] = s[nb + 1 + k] / n;
+      if (out->se_R_k) out->se_R_k[i * K + k] = se_of(s[nb + 1 + k], s2[nb + 1 + k], n);
+    }
+    const int o1 = nb + 1 + K;
+    if (out->R1) out->R1[i] = s[o1] / n;
+    if (out->se_R1) out->se_R1[i] = se_of(s[o1], s2[o1], n);
+    if (out->T) out->T[i] = s[o1 + 1] / n;
+    if (out->se_T) out->se_T[i] = se_of(s[o1 + 1], s2[o1 + 1], n);
+    if (out->A) out->A[i] = s[o1 + 2] / n;
+    if (out->se_A) out->se_A[i] = se_of(s[o1 + 2], s2[o1 + 2], n);
+    if (out->truncated) out->truncated[i] = s[o1 + 3];
+    if (out->steps) out->steps[i] = s[o1 + 4] / n;
+    free(s); free(s2);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Score-function gradient (differentiating the path contribution f_SSS of  */
+/* Sec. 4.1 and the mixture of Eq. 4).                                        */
+/* ------------------------------------------------------------------------ */
+/* For a path that chose medium k, made n collisions, travelled L and
+ * scattered with cosines mu_i, the log-density of its geometry and its
+ * throughput alpha^n give
+ *   d/d alpha_k   :  n / alpha_k
+ *   d/d sigma_t,k :  n / sigma_t,k - L
+ *   d/d g_k       :  sum_i d log p_HG(mu_i; g_k) / d g_k
+ *   d/d w_k       :  1 / p_k with p_k = w_k / sum(w)   (the partial of
+ *                     sum_k w_k S_k with the others held fixed, i.e. S_k)
+ * each multiplied by the path's exit weight and by the upstream derivative
+ * of the loss with respect to the tally the path landed in:
+ *   top exit   : grad_R + grad_bins[bin] (0 for overflow) + grad_R_k[k]
+ *   bottom exit: grad_T
+ * Roulette and analog absorption change only the sampling of the weight,
+ * whose conditional mean given the geometry is the analog throughput, so
+ * they add no score term.  Outputs d_* are [K][n_inst] and hold the mean
+ * over the instance's N paths. */
+int oracle_walk_grad(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
+                     const float* g, const float* w, const uint32_t* n_paths,
+                     const float* thickness_mm, double n_rel, const oracle_opts* o,
+                     const double* grad_R, const double* grad_bins,
+                     const double* grad_R_k, const double* grad_T,
+                     double* d_alpha, double* d_sigma_t, double* d_g, double* d_w,
+                     double* se_d_alpha, double* se_d_sigma_t, double* se_d_g,
+                     double* se_d_w) {
+  if (K < 1 || K > ORC_KMAX || o->nbins < 1) return 1;
+  const int nb = o->nbins;
+  for (int64_t i = 0; i < n_inst; ++i) {
+    const uint32_t N = n_paths[i];
+    const double d = thickness_mm ? (double)thickness_mm[i] : INFINITY;
+    double wsum = 0.0;
+    float wk[ORC_KMAX];
+    for (int k = 0; k < K; ++k) { wk[k] = w[(int64_t)k * n_inst + i]; wsum += wk[k]; }
+    const int64_t nch = ((int64_t)N + ORC_CHUNK - 1) / ORC_CHUNK;
+    double* ps = calloc((size_t)(nch > 0 ? nch : 1) * 8 * ORC_KMAX, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      double* ls = ps + (size_t)ch * 8 * ORC_KMAX;
+      double* ls2 = ls + 4 * ORC_KMAX;
+      const int64_t p1 = (ch + 1) * ORC_CHUNK < (int64_t)N ? (ch + 1) * ORC_CHUNK : (int64_t)N;
+      for (int64_t p = ch * ORC_CHUNK; p < p1; ++p) {
+        oracle_path r;
+        oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i, (uint32_t)p, d, n_rel,
+                          o, &r);
+        double v = 0.0;
+        if (r.exit_kind == 0) {
+          if (grad_R) v += grad_R[i];
+          if (grad_bins && r.bin < nb) v += grad_bins[i * nb + r.bin];
+          if (grad_R_k) v += grad_R_k[i * K + r.medium];
+        } else if (r.exit_kind == 1) {
+          if (grad_T) v += grad_T[i];
+        }
+        double c[4 * ORC_KMAX] = {0};
+        if (v != 0.0) {
+          const int k = r.medium;
+          const double a = alpha[(int64_t)k * n_inst + i];
+          const double st = sigma_t[(int64_t)k * n_inst + i];
+          const double Wv = r.weight * v;
+          c[0 * K + k] = Wv * (double)r.n_coll / a;
+          c[1 * K + k] = Wv * ((double)r.n_coll / st - r.length);
+          c[2 * K + k] = Wv * r.dlogp_dg;
+          c[3 * K + k] = Wv * wsum / (double)wk[k];
+        }
+        for (int j = 0; j < 4 * K; ++j) { ls[j] += c[j]; ls2[j] += c[j] * c[j]; }
+      }
+    }
+    double s[4 * ORC_KMAX] = {0}, s2[4 * ORC_KMAX] = {0};
+    for (int64_t ch = 0; ch < nch; ++ch)
+      for (int j = 0; j < 4 * K; ++j) {
+        s[j] += ps[(size_t)ch * 8 * ORC_KMAX + (size_t)j];
+        s2[j] += ps[(size_t)ch * 8 * ORC_KMAX + 4 * ORC_KMAX + (size_t)j];
+      }
+    free(ps);
+    const double n = (double)N;
+    double* outs[4] = {d_alpha, d_sigma_t, d_g, d_w};
+    double* ses[4] = {se_d_alpha, se_d_sigma_t, se_d_g, se_d_w};
+    for (int q = 0; q < 4; ++q)
+      for (int k = 0; k < K; ++k) {
+        if (outs[q]) outs[q][(int64_t)k * n_inst + i] = s[q * K + k] / n;
+        if (ses[q]) ses[q][(int64_t)k * n_inst + i] = se_of(s[q * K + k], s2[q * K + k], n);
+      }
+  }
+  return 0;
+}
+
+/* Per-path trace for a list of (instance, path) pairs: lets tests compare a
+ * sampled subset of a full-size run one path at a time. */
+int oracle_trace_many(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
+                      const float* g, const float* w, const float* thickness_mm,
+                      double n_rel, const oracle_opts* o, int64_t n_query,
+                      const int64_t* q_inst, const uint32_t* q_path, oracle_path* res) {
+  if (K < 1 || K > ORC_KMAX) return 1;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < n_query; ++q) {
+    const int64_t i = q_inst[q];
+    const double d = thickness_mm ? (double)thickness_mm[i] : INFINITY;
+    oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i, q_path[q], d, n_rel, o, &res[q]);
+  }
+  return 0;
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
