@@ -30,7 +30,9 @@
  * definition, with the same counter layout:
  *     key     = (seed_lo, seed_hi)
  *     counter = (step, path, instance, tag)   tag 0 = walk step, 1 = selection
- * and the same 24-bit uniform u = ((x >> 8) + 0.5) * 2^-24 in (0,1).
+ * and the same 23-bit uniform u = ((x >> 9) + 0.5) * 2^-23 in (0,1), which
+ * is exact in binary32 as well as binary64 (a 24-bit version would round
+ * to 1.0 in binary32 at the top of its range).
  * Everything else (flights, Fresnel, HG, rotation, weights, tallies) is
  * double precision here, so GPU-vs-oracle differences come only from the
  * kernel's binary32 rounding.  The one integer decision that floating point
@@ -78,8 +80,8 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* 24-bit uniform strictly inside (0,1): never 0 (so -ln u is finite), never 1. */
-static double u24(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* 23-bit uniform strictly inside (0,1): never 0 (so -ln u is finite), never 1. */
+static double u23(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 static void draw4(uint64_t seed, uint32_t step, uint32_t path, uint32_t inst,
                   uint32_t tag, double u[4]) {
@@ -87,7 +89,7 @@ static void draw4(uint64_t seed, uint32_t step, uint32_t path, uint32_t inst,
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t x[4];
   oracle_philox4x32_10(ctr, key, x);
-  for (int i = 0; i < 4; ++i) u[i] = u24(x[i]);
+  for (int i = 0; i < 4; ++i) u[i] = u23(x[i]);
 }
 
 /* ------------------------------------------------------------------------ */
