@@ -1,0 +1,325 @@
+"""Benchmark of the mixture-of-media random walk on B300.
+
+One step = one sss_walk over the spectral workload: a 256 x 256 texel
+parameter field x 81 bands (380-780 nm), three media per texel and band,
+4096 paths per instance, 64 radial bins over 10 mm, semi-infinite slab with
+n = 1.4 (Fresnel faces).  The metric is paths/s on the whole job.  Beside it:
+the same metric end to end through the public API with host buffers, the
+adjoint/forward time ratio on the adjoint workload (64 x 64 x 81 at 2^16
+paths), the ALU roofline of the walk kernel and the FP64 oracle timed on the
+host cores on a sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+Under torchrun (N > 1) every rank walks its own field of the same size
+(weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mixture random-walk paths/s on 1 B300 (81 bands); adjoint/forward time ratio"
+UNIT = "paths/s"
+WORKLOAD = dict(workload="spectral_field_256x256x81", texels=256 * 256, bands=81,
+                paths_per_instance=4096, nbins=64, r_max_mm=10.0, n_rel=1.4,
+                slab="semi-infinite", K=3, param_seed=1, walk_seed=1001)
+# Algorithmic lane-operations of one walk step (one Philox block plus the
+# step's floating-point work); derivation in the design notes.
+ALG_ALU_OPS_PER_STEP = 120
+ALG_MUFU_OPS_PER_STEP = 6
+SM_LANES_PER_CLK = 128
+MUFU_LANES_PER_CLK = 16
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def spectral_inputs(rank):
+    from paper_2606_27604_b300 import inputs
+    return inputs.spectral_field(n_texels=WORKLOAD["texels"],
+                                 param_seed=WORKLOAD["param_seed"] + rank,
+                                 n_paths=WORKLOAD["paths_per_instance"], n_rel=1.4)
+
+
+def cpu_baseline_sample(n_texels=24):
+    """The FP64 oracle on a bounded sample of the workload (host cores)."""
+    import oracle
+    from paper_2606_27604_b300 import inputs
+    x = inputs.spectral_field(n_texels=n_texels, param_seed=WORKLOAD["param_seed"],
+                              n_paths=WORKLOAD["paths_per_instance"], n_rel=1.4)
+    o = oracle.OracleOpts(nbins=64, r_max_mm=10.0, seed=WORKLOAD["walk_seed"])
+    t0 = time.perf_counter()
+    oracle.walk(x.alpha, x.sigma_t, x.g, x.w, x.n_paths, None, x.n_rel, o)
+    dt = time.perf_counter() - t0
+    paths = int(x.n_paths.sum())
+    return {"value": paths / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_texels} texels x 81 bands x 4096 paths ({paths} paths) of the "
+                      f"spectral workload, FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    per_step = []
+    for _ in range(args.warmup):
+        cpu_baseline_sample(args.ref_texels)
+    res = None
+    for _ in range(args.steps):
+        res = cpu_baseline_sample(args.ref_texels)
+        per_step.append(res["value"])
+    v = float(np.mean(per_step))
+    paths_per_step = args.ref_texels * 81 * 4096
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": paths_per_step / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, sample_texels=args.ref_texels),
+            "cpu_baseline": dict(res, value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--ref-texels", type=int, default=16)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2606_27604_b300 import api
+
+    x = spectral_inputs(rank)
+    m = api.Media.from_inputs(x, device=dev)
+    o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=WORKLOAD["walk_seed"] + 7919 * rank)
+    wsp = api.alloc_workspace(m, o)
+    out = api.alloc_tallies(m, o)
+    stream = torch.cuda.current_stream(dev)
+    paths_per_step = int(x.n_paths.astype(np.int64).sum())
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        api.walk(m, o, workspace=wsp, out=out)
+    torch.cuda.synchronize()
+    code, flags = api.read_status(wsp)
+    if code != 0:
+        raise RuntimeError(f"walk status {code} flags {flags}")
+
+    # ---- device-timed region: inputs resident in HBM ----------------------
+    k_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k_stop = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for e in k_start + k_stop:
+        e.record(stream)   # creates the CUDA events
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    for i in range(args.steps):
+        api.profile_events(k_start[i], k_stop[i])
+        api.walk(m, o, workspace=wsp, out=out)
+    api.profile_events(None, None)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    kern = [a.elapsed_time(b) / 1e3 for a, b in zip(k_start, k_stop)]
+    if dist is not None:
+        tt = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    total_paths = paths_per_step * args.steps * ws
+    value = total_paths / elapsed
+    steps_mean = float(out["steps"].mean().item())
+    total_draws = float(out["steps"].double().sum().item()) * WORKLOAD["paths_per_instance"]
+    code, flags = api.read_status(wsp)
+
+    # ---- end to end through the API with host buffers ---------------------
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(getattr(x, k))).pin_memory()
+                for k in ("alpha", "sigma_t", "g", "w")}
+        res_host = {k: torch.empty(out[k].shape, dtype=out[k].dtype).pin_memory()
+                    for k in ("R", "bins")}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = sum(v.numel() * v.element_size() for v in res_host.values())
+        dm = api.Media(*(torch.empty_like(getattr(m, k)) for k in ("alpha", "sigma_t", "g", "w")),
+                       n_paths=None, uniform_paths=m.uniform_paths, n_rel=m.n_rel)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for k in ("alpha", "sigma_t", "g", "w"):
+                getattr(dm, k).copy_(host[k], non_blocking=True)
+            api.walk(dm, o, workspace=wsp, out=out)
+            for k in res_host:
+                res_host[k].copy_(out[k], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        et = e0.elapsed_time(e1) / 1e3
+        if dist is not None:
+            tt = torch.tensor([et], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            et = float(tt.item())
+        e2e = {"value": total_paths / et, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+        del dm
+
+    # ---- adjoint / forward ratio on the adjoint workload ------------------
+    ratio = None
+    if not args.no_adjoint:
+        del wsp, out
+        torch.cuda.empty_cache()
+        from paper_2606_27604_b300 import inputs
+        xa = inputs.spectral_field(n_texels=64 * 64, param_seed=3 + rank, n_paths=1 << 16)
+        ma = api.Media.from_inputs(xa, device=dev)
+        oa = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1003)
+        wa = api.alloc_workspace(ma, oa)
+        wb = api.alloc_workspace(ma, oa, adjoint=True)
+        oa_out = api.alloc_tallies(ma, oa)
+        gen = torch.Generator(device=dev).manual_seed(3)
+        gR = torch.randn(ma.n_inst, device=dev, dtype=torch.float64, generator=gen)
+        gB = torch.randn(ma.n_inst, 64, device=dev, dtype=torch.float64, generator=gen)
+        grads = None
+        api.walk(ma, oa, workspace=wa, out=oa_out)
+        grads = api.walk_bwd(ma, oa, grad_R=gR, grad_bins=gB, workspace=wb)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        api.walk(ma, oa, workspace=wa, out=oa_out)
+        ev[1].record(stream)
+        ev[2].record(stream)
+        api.walk_bwd(ma, oa, grad_R=gR, grad_bins=gB, workspace=wb, out=grads)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        tf, tb = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+        ratio = {"value": tb / tf, "fwd_ms": tf, "bwd_ms": tb,
+                 "workload": "spectral_field_64x64x81 at 65536 paths, grads w.r.t. "
+                             "(alpha, sigma_t, g, w) x 3 from upstream on R and 64 bins"}
+
+    # ---- roofline of the walk kernel --------------------------------------
+    kmean = float(np.mean(kern))
+    f_mhz = clk["sm_mhz"] if clk else 2032.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * SM_LANES_PER_CLK * f_mhz * 1e6 / 1e12
+    achieved = total_draws * ALG_ALU_OPS_PER_STEP / kmean / 1e12
+    mufu = total_draws * ALG_MUFU_OPS_PER_STEP / kmean / (sms * MUFU_LANES_PER_CLK * f_mhz * 1e6)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "walk_persistent_kernel<false>",
+                "peak_basis": f"{sms} SMs x {SM_LANES_PER_CLK} FP32/INT32 lanes/clk x "
+                              f"{f_mhz:.0f} MHz (median SM clock sampled in the timed region)",
+                "ops_per_step": ALG_ALU_OPS_PER_STEP, "steps_per_launch": total_draws,
+                "mufu_frac": mufu, "kernel_ms": kmean * 1e3}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism=f"replicas{ws}",
+                           l2="inputs (255 MB) and tally workspace (5.9 GB) exceed the 126 MB L2",
+                           steps_per_path=steps_mean),
+            "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "adjoint_forward_ratio": ratio, "status_flags": flags}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,255 @@
+/*
+ * sss.h -- C ABI of libsss: the mixture-of-media subsurface random walk on
+ * NVIDIA B300 (sm_103a).
+ *
+ * The library evaluates, for many independent instances (texel x
+ * wavelength), the radial subsurface profile of a K-media mixture
+ * (paper: Sec. 4.1, Eq. 3 radial form R_d(r) = R * P_d(r) under normal
+ * incidence; Eq. 4 mixture S = sum_k w_k S_k with sum_k w_k = 1), by a Monte
+ * Carlo random walk that picks one medium per path with probability w_k
+ * before the walk starts (Sec. 4.1, Sec. 6, Sec. 7).  Media are given by
+ * single-scattering albedo alpha, extinction sigma_t and Henyey-Greenstein
+ * anisotropy g (the parameter set theta(lambda) of Sec. 5.1, Eq. 10).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every pointer named "device" must point to memory of the CUDA device
+ *    that is current on the calling thread.  The library never allocates
+ *    device memory: the caller owns every buffer, including the workspace.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and runs asynchronously: results are valid once the stream has
+ *    reached the call's end.
+ *  - Errors a host can see (NULL pointer where one is required, sizes out of
+ *    range, misaligned pointers, too small workspace) are returned at once
+ *    and nothing is enqueued.  Errors only the device can see (invalid
+ *    parameter values, step-cap truncation, fixed-point overflow) set bits
+ *    of a status word kept in the workspace; read it with sss_read_status.
+ *    No kernel traps and no kernel waits on another kernel.
+ *  - When a status other than SSS_OK is returned or flagged, the outputs
+ *    are undefined.
+ *  - Calls that share a workspace must not overlap on the GPU.
+ */
+#ifndef SSS_H_
+#define SSS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SSS_ABI_VERSION 1
+#define SSS_KMAX 4          /* media per mixture supported (the paper uses 3) */
+#define SSS_NBINS_MAX 1024  /* radial bins supported */
+
+typedef enum {
+  SSS_OK = 0,
+  SSS_ERR_INVALID_ARG = 1,  /* host-detected bad argument */
+  SSS_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  SSS_ERR_WORKSPACE = 3,    /* workspace smaller than sss_*_workspace_size */
+  SSS_ERR_STEP_LIMIT = 4,   /* device: some paths hit the step cap */
+  SSS_ERR_OVERFLOW = 5,     /* device: a fixed-point accumulator saturated */
+  SSS_ERR_DEVICE_PARAM = 6, /* device: a parameter value is out of range */
+  SSS_ERR_UNSUPPORTED = 7   /* no sm_103a device, or a feature not built */
+} sss_status;
+
+/* Device status word bits (sss_read_status). */
+#define SSS_FLAG_PARAM 0x1u      /* alpha, sigma_t, g, w or thickness invalid */
+#define SSS_FLAG_STEP_LIMIT 0x2u /* at least one path was truncated */
+#define SSS_FLAG_OVERFLOW 0x4u   /* a gradient accumulator saturated */
+#define SSS_FLAG_ZERO_WEIGHT 0x8u /* a medium with w_k = 0 got a zero gradient */
+
+typedef void* sss_stream_t; /* cudaStream_t */
+
+/* Per-instance media.  Arrays are structure-of-arrays [K][n_inst], float32,
+ * device, 4-byte aligned: element (k, i) is at [k * n_inst + i].
+ *   alpha   in [0, 1]          single-scattering albedo
+ *   sigma_t > 0, finite        extinction, mm^-1 (positions are in mm)
+ *   g       in (-1, 1)         Henyey-Greenstein mean cosine
+ *   w       >= 0, sum_k w = 1 (within 1e-5)   mixture weight (Eq. 4)
+ * n_paths: device uint32 [n_inst] path budget per instance, or NULL to use
+ *          uniform_paths for every instance.
+ * thickness_mm: device float32 [n_inst] slab thickness (> 0; +inf for a
+ *          semi-infinite slab), or NULL for all semi-infinite.
+ * n_rel:   refractive index of the media relative to the outside (>= 1).
+ * K in [1, SSS_KMAX]; n_inst in [0, 2^32). */
+typedef struct {
+  const float* alpha;
+  const float* sigma_t;
+  const float* g;
+  const float* w;
+  const uint32_t* n_paths;
+  uint32_t uniform_paths;
+  const float* thickness_mm;
+  float n_rel;
+  int32_t K;
+  int64_t n_inst;
+} sss_params;
+
+/* Walk options (a zero-filled struct is NOT valid: call sss_walk_opts_default).
+ *   nbins, r_max_mm : linear radial bins over [0, r_max) in the entry face;
+ *                     exits at r >= r_max go to the overflow tally.
+ *   mode            : 0 = albedo weighting with Russian roulette (default),
+ *                     1 = analog absorption.
+ *   rr_threshold    : roulette weight W_th (mode 0); a path whose weight
+ *                     falls below it survives with probability W/W_th at
+ *                     weight W_th.  0 disables roulette.
+ *   entry_fresnel   : 1 = entry weight 1 - R0, R0 = ((n-1)/(n+1))^2: the
+ *                     specular reflection is excluded from every tally.
+ *   max_steps       : cap on random-number draws per path (a path that hits
+ *                     it is dropped and counted in `truncated`).
+ *   seed            : 64-bit Philox key.
+ *   path_offset     : index of the first path of each instance; runs over
+ *                     [0, M) and [M, N) add up bit-exactly to [0, N).
+ *   want_sumsq      : 1 = also tally squared exit weights (standard errors).
+ *   schedule        : 0 = persistent batched kernel over all instances;
+ *                     1 = plain baseline, one launch per instance, one thread
+ *                     per path, no regrouping.
+ *   use_graph       : 1 = capture the call's launches once in a CUDA graph
+ *                     (cached per argument set) and replay it.
+ *   block_threads, unit_paths, regroup : launch shape of the persistent
+ *                     kernel (0 = built-in defaults); results do not depend
+ *                     on them. */
+typedef struct {
+  int32_t nbins;
+  float r_max_mm;
+  int32_t mode;
+  float rr_threshold;
+  int32_t entry_fresnel;
+  uint32_t max_steps;
+  uint64_t seed;
+  uint32_t path_offset;
+  int32_t want_sumsq;
+  int32_t schedule;
+  int32_t use_graph;
+  int32_t block_threads;
+  int32_t unit_paths;
+  int32_t regroup;
+} sss_walk_opts;
+
+/* Forward outputs, all float64 device arrays owned by the caller; any may be
+ * NULL.  Each tally is the mean over the instance's N paths of that path's
+ * exit weight (a fraction of the incident power):
+ *   R [n_inst]         diffuse reflectance through the entry face (= sum of
+ *                      bins + overflow), the "R" of Eq. 3
+ *   T [n_inst]         transmittance through the far face of a finite slab
+ *   A [n_inst]         absorbed weight
+ *   bins [n_inst][nbins]  radial exit histogram (R * P_d(r) integrated over
+ *                      each annulus)
+ *   overflow [n_inst]  exits at r >= r_max
+ *   R_k [n_inst][K]    reflectance carried by paths that chose medium k
+ *   R1 [n_inst]        reflectance of paths with exactly one collision
+ *   stderr_R, stderr_bins: standard errors (need want_sumsq = 1)
+ *   truncated [n_inst] uint64 count of paths cut by max_steps
+ *   steps [n_inst]     mean random-number draws (walk steps) per path
+ *   raw [n_inst][sss_tally_count(nbins, K, want_sumsq)] uint64: the exact
+ *                      fixed-point sums (weight * 2^32) in the order
+ *                      bins, overflow, R_k, R1, T, A, then the plain counts
+ *                      truncated and steps, then [sumsq bins, sumsq overflow]
+ *                      (squared weights * 2^32). */
+typedef struct {
+  double* R;
+  double* T;
+  double* A;
+  double* bins;
+  double* overflow;
+  double* R_k;
+  double* R1;
+  double* stderr_R;
+  double* stderr_bins;
+  uint64_t* truncated;
+  double* steps;
+  uint64_t* raw;
+} sss_tallies;
+
+/* Upstream derivatives d(loss)/d(tally) for sss_walk_bwd; float64 device,
+ * any may be NULL (= zero):  grad_R [n_inst], grad_bins [n_inst][nbins],
+ * grad_R_k [n_inst][K], grad_T [n_inst]. */
+typedef struct {
+  const double* grad_R;
+  const double* grad_bins;
+  const double* grad_R_k;
+  const double* grad_T;
+} sss_grad_in;
+
+/* Parameter gradients, float64 device [K][n_inst], any may be NULL.
+ * d_w is the partial derivative of sum_k w_k S_k with the other weights
+ * held fixed (Eq. 4), i.e. the medium's own contribution S_k; project onto
+ * the simplex (subtract the w-weighted mean) for a constrained step. */
+typedef struct {
+  double* d_alpha;
+  double* d_sigma_t;
+  double* d_g;
+  double* d_w;
+} sss_grad_out;
+
+/* Fill *o with the defaults: 64 bins over 10 mm, mode 0, W_th = 1/16,
+ * entry_fresnel 1, max_steps 65536, seed 0, want_sumsq 1, schedule 0,
+ * use_graph 0, automatic launch shape. */
+void sss_walk_opts_default(sss_walk_opts* o);
+
+/* Number of uint64 tallies per instance in the raw layout above. */
+int32_t sss_tally_count(int32_t nbins, int32_t K, int32_t want_sumsq);
+
+/* Workspace bytes sss_walk / sss_walk_bwd need for these arguments
+ * (256-byte aligned device memory; contents need not be initialised).
+ * Returns 0 if the arguments are invalid. */
+size_t sss_walk_workspace_size(const sss_params* p, const sss_walk_opts* o);
+size_t sss_walk_bwd_workspace_size(const sss_params* p, const sss_walk_opts* o);
+
+/* Forward walk (Sec. 4.1 Eq. 2-4; medium choice per Sec. 7).  Enqueues
+ * parameter validation, the walk and the float64 finalisation on `stream`.
+ * Results are bit-identical for identical arguments, whatever the launch
+ * shape.  Returns SSS_ERR_INVALID_ARG / SSS_ERR_WORKSPACE / SSS_ERR_CUDA /
+ * SSS_ERR_UNSUPPORTED as described above; device-side problems are
+ * reported through sss_read_status. */
+sss_status sss_walk(const sss_params* p, const sss_walk_opts* o, void* workspace,
+                    size_t workspace_bytes, sss_tallies* out, sss_stream_t stream);
+
+/* Path-replay adjoint of sss_walk: re-runs every path from its Philox
+ * counters (no stored path state) and accumulates, for each path, its exit
+ * weight times the upstream derivative of the tally it landed in times the
+ * score of the path density (differentiating f_SSS of Sec. 4.1 and the
+ * mixture of Eq. 4):
+ *   d/d alpha_k : n / alpha_k           (n collisions)
+ *   d/d sigma_t,k : n / sigma_t,k - L   (L = path length inside)
+ *   d/d g_k     : sum_i d log p_HG(mu_i; g_k) / d g_k
+ *   d/d w_k     : sum(w) / w_k          (paths that chose k)
+ * Must get the same p and o (seed, path_offset, ...) as the forward call.
+ * Requires mode 0 or 1; roulette is allowed. */
+sss_status sss_walk_bwd(const sss_params* p, const sss_walk_opts* o, void* workspace,
+                        size_t workspace_bytes, const sss_grad_in* gin,
+                        sss_grad_out* gout, sss_stream_t stream);
+
+/* Waits for `stream`, then returns the status word the last call that used
+ * `workspace` left (SSS_FLAG_* bits) in *flags and maps it to a status:
+ * SSS_ERR_DEVICE_PARAM, SSS_ERR_OVERFLOW, SSS_ERR_STEP_LIMIT or SSS_OK. */
+sss_status sss_read_status(const void* workspace, sss_stream_t stream, uint32_t* flags);
+
+/* Philox4x32-10 blocks computed by the device code the walk uses
+ * (diagnostic): out[4*i .. 4*i+3] = Philox(ctr[4*i .. 4*i+3], key).
+ * ctr, out: device uint32 arrays of 4*n words. */
+sss_status sss_philox(const uint32_t* ctr, uint64_t key, int64_t n, uint32_t* out,
+                      sss_stream_t stream);
+
+/* Profiling hook.  With both events non-NULL (cudaEvent_t handles created by
+ * the caller), each following sss_walk / sss_walk_bwd issued from this host
+ * thread records `start` right before and `stop` right after its main walk
+ * kernel, on the call's stream, so the caller can time that kernel alone.
+ * Pass NULL, NULL to stop.  Ignored for calls replayed from a cached graph. */
+void sss_profile_events(void* start, void* stop);
+
+/* Drops every cached CUDA graph (use_graph = 1). */
+void sss_release_plans(void);
+
+/* Static text for a status code. */
+const char* sss_status_string(sss_status s);
+
+/* SSS_ABI_VERSION of the loaded library. */
+int32_t sss_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSS_H_ */

@@ -126,10 +126,20 @@ def select_medium(w, u: float) -> int:
     return _load().oracle_select_medium(_p(w), len(w), u)
 
 
+def _ids(inst_ids, n):
+    if inst_ids is None:
+        return None
+    a = np.ascontiguousarray(inst_ids, dtype=np.int64)
+    assert a.shape == (n,)
+    return a
+
+
 def walk(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
-         opts: OracleOpts = OracleOpts(), path_offset: int = 0) -> dict:
+         opts: OracleOpts = OracleOpts(), path_offset: int = 0, inst_ids=None) -> dict:
     """Mean tallies per instance (fractions of incident power) and their
-    standard errors; see ``oracle_walk`` in ``walk_oracle.c``."""
+    standard errors; see ``oracle_walk`` in ``walk_oracle.c``.  ``inst_ids``
+    re-walks a subset of a larger batch under the instance numbers the
+    random-number counters had there."""
     alpha, sigma_t, g, w, K, n = _check(alpha, sigma_t, g, w)
     n_paths = np.ascontiguousarray(n_paths, dtype=np.uint32)
     assert n_paths.shape == (n,)
@@ -142,10 +152,11 @@ def walk(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
     res["R_k"] = np.zeros((n, K))
     res["se_R_k"] = np.zeros((n, K))
     out = _Out(**{k: _p(v) for k, v in res.items()})
+    ids = _ids(inst_ids, n)
     o = opts._c()
     rc = _load().oracle_walk(C.c_int64(n), C.c_int(K), _p(alpha), _p(sigma_t), _p(g),
                              _p(w), _p(n_paths), _p(th), C.c_double(n_rel), C.byref(o),
-                             C.c_uint32(path_offset), C.byref(out))
+                             C.c_uint32(path_offset), _p(ids), C.byref(out))
     if rc != 0:
         raise ValueError("oracle_walk rejected its arguments")
     return res
@@ -153,7 +164,7 @@ def walk(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
 
 def walk_grad(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
               opts: OracleOpts = OracleOpts(), grad_R=None, grad_bins=None,
-              grad_R_k=None, grad_T=None) -> dict:
+              grad_R_k=None, grad_T=None, inst_ids=None) -> dict:
     """Score-function gradient of sum(upstream * tallies) w.r.t. the
     per-medium parameters, shape [K][n_inst] each, with standard errors."""
     alpha, sigma_t, g, w, K, n = _check(alpha, sigma_t, g, w)
@@ -175,7 +186,8 @@ def walk_grad(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
     o = opts._c()
     rc = _load().oracle_walk_grad(
         C.c_int64(n), C.c_int(K), _p(alpha), _p(sigma_t), _p(g), _p(w), _p(n_paths),
-        _p(th), C.c_double(n_rel), C.byref(o), _p(gR), _p(gB), _p(gK), _p(gT),
+        _p(th), C.c_double(n_rel), C.byref(o), _p(_ids(inst_ids, n)),
+        _p(gR), _p(gB), _p(gK), _p(gT),
         *[_p(res[k]) for k in ("d_alpha", "d_sigma_t", "d_g", "d_w",
                                "se_d_alpha", "se_d_sigma_t", "se_d_g", "se_d_w")])
     if rc != 0:

@@ -194,16 +194,19 @@ typedef struct {
   double x, y;      /* exit point on the face */
 } oracle_path;
 
+/* inst indexes the parameter arrays; rng_inst is the instance number the
+ * random-number counters use (the same unless a subset of a larger batch is
+ * being re-walked). */
 void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
                        const float* w, int K, int64_t n_inst, int64_t inst,
-                       uint32_t path, double thickness_mm, double n_rel,
+                       uint32_t rng_inst, uint32_t path, double thickness_mm, double n_rel,
                        const oracle_opts* o, oracle_path* res) {
   double u[4];
   memset(res, 0, sizeof(*res));
   /* Medium selection once per path, before the walk (Eq. 4, Sec. 7). */
   float wk[ORC_KMAX];
   for (int k = 0; k < K; ++k) wk[k] = w[(int64_t)k * n_inst + inst];
-  draw4(o->seed, 0u, path, (uint32_t)inst, 1u, u);
+  draw4(o->seed, 0u, path, rng_inst, 1u, u);
   int k = oracle_select_medium(wk, K, u[0]);
   res->medium = k;
   double a = alpha[(int64_t)k * n_inst + inst];
@@ -221,7 +224,7 @@ void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
   uint32_t step = 0;
   for (;;) {
     if (step >= o->max_steps) { res->exit_kind = 3; break; }
-    draw4(o->seed, step, path, (uint32_t)inst, 0u, u);
+    draw4(o->seed, step, path, rng_inst, 0u, u);
     step++;
     double s = -log(u[0]) / st; /* exponential free flight (transmittance T) */
     double db = INFINITY;
@@ -278,7 +281,8 @@ void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
  *   se_R_k : [n_inst][K]
  * Each tally is the mean over the instance's N paths of the per-path
  * contribution (a fraction of the incident power); se_* is the sample
- * standard error of that mean. */
+ * standard error of that mean.  inst_ids (or NULL) gives the instance number
+ * each array column had in the batch it was drawn from, for the counters. */
 typedef struct {
   double *R, *T, *A, *bins, *overflow, *R_k, *R1, *truncated;
   double *se_R, *se_T, *se_A, *se_bins, *se_R_k, *se_R1;
@@ -295,7 +299,7 @@ static double se_of(double s, double s2, double n) {
 int oracle_walk(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
                 const float* g, const float* w, const uint32_t* n_paths,
                 const float* thickness_mm, double n_rel, const oracle_opts* o,
-                uint32_t path_offset, oracle_out* out) {
+                uint32_t path_offset, const int64_t* inst_ids, oracle_out* out) {
   if (K < 1 || K > ORC_KMAX || o->nbins < 1 || o->nbins > ORC_NBINS_MAX) return 1;
   const int nb = o->nbins;
   /* per-path vector: [bins nb][overflow][R_k K][R1][T][A][trunc][steps] */
@@ -316,6 +320,7 @@ int oracle_walk(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
       for (int64_t p = ch * ORC_CHUNK; p < p1; ++p) {
         oracle_path r;
         oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i,
+                          inst_ids ? (uint32_t)inst_ids[i] : (uint32_t)i,
                           path_offset + (uint32_t)p, d, n_rel, o, &r);
         memset(c, 0, sizeof(double) * (size_t)nv);
         if (r.exit_kind == 0) {
@@ -392,6 +397,7 @@ int oracle_walk(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
 int oracle_walk_grad(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
                      const float* g, const float* w, const uint32_t* n_paths,
                      const float* thickness_mm, double n_rel, const oracle_opts* o,
+                     const int64_t* inst_ids,
                      const double* grad_R, const double* grad_bins,
                      const double* grad_R_k, const double* grad_T,
                      double* d_alpha, double* d_sigma_t, double* d_g, double* d_w,
@@ -414,8 +420,9 @@ int oracle_walk_grad(int64_t n_inst, int K, const float* alpha, const float* sig
       const int64_t p1 = (ch + 1) * ORC_CHUNK < (int64_t)N ? (ch + 1) * ORC_CHUNK : (int64_t)N;
       for (int64_t p = ch * ORC_CHUNK; p < p1; ++p) {
         oracle_path r;
-        oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i, (uint32_t)p, d, n_rel,
-                          o, &r);
+        oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i,
+                          inst_ids ? (uint32_t)inst_ids[i] : (uint32_t)i, (uint32_t)p, d,
+                          n_rel, o, &r);
         double v = 0.0;
         if (r.exit_kind == 0) {
           if (grad_R) v += grad_R[i];
@@ -468,7 +475,8 @@ int oracle_trace_many(int64_t n_inst, int K, const float* alpha, const float* si
   for (int64_t q = 0; q < n_query; ++q) {
     const int64_t i = q_inst[q];
     const double d = thickness_mm ? (double)thickness_mm[i] : INFINITY;
-    oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i, q_path[q], d, n_rel, o, &res[q]);
+    oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i, (uint32_t)i, q_path[q], d, n_rel, o,
+                      &res[q]);
   }
   return 0;
 }

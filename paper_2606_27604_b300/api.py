@@ -1,0 +1,311 @@
+"""Python binding of libsss (include/sss.h): argument marshalling only.
+
+Every step of the walk runs in the library's CUDA kernels; this module only
+turns torch CUDA tensors into the C structs and pointers the C ABI takes.
+Importing it loads ``libsss.so`` and raises if the library is missing --
+there is no CPU fallback.
+"""
+import ctypes as C
+import os
+from dataclasses import dataclass, asdict
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsss.so")
+
+SSS_OK = 0
+STATUS_NAMES = {0: "SSS_OK", 1: "SSS_ERR_INVALID_ARG", 2: "SSS_ERR_CUDA",
+                3: "SSS_ERR_WORKSPACE", 4: "SSS_ERR_STEP_LIMIT", 5: "SSS_ERR_OVERFLOW",
+                6: "SSS_ERR_DEVICE_PARAM", 7: "SSS_ERR_UNSUPPORTED"}
+FLAG_PARAM, FLAG_STEP_LIMIT, FLAG_OVERFLOW, FLAG_ZERO_WEIGHT = 0x1, 0x2, 0x4, 0x8
+
+
+class SSSError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)} ({_status_string(code)})")
+
+
+class Params(C.Structure):
+    _fields_ = [("alpha", C.c_void_p), ("sigma_t", C.c_void_p), ("g", C.c_void_p),
+                ("w", C.c_void_p), ("n_paths", C.c_void_p), ("uniform_paths", C.c_uint32),
+                ("thickness_mm", C.c_void_p), ("n_rel", C.c_float), ("K", C.c_int32),
+                ("n_inst", C.c_int64)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("nbins", C.c_int32), ("r_max_mm", C.c_float), ("mode", C.c_int32),
+                ("rr_threshold", C.c_float), ("entry_fresnel", C.c_int32),
+                ("max_steps", C.c_uint32), ("seed", C.c_uint64), ("path_offset", C.c_uint32),
+                ("want_sumsq", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
+                ("block_threads", C.c_int32), ("unit_paths", C.c_int32),
+                ("regroup", C.c_int32)]
+
+
+class Tallies(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("R", "T", "A", "bins", "overflow", "R_k", "R1",
+                                          "stderr_R", "stderr_bins", "truncated", "steps",
+                                          "raw")]
+
+
+class GradIn(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("grad_R", "grad_bins", "grad_R_k", "grad_T")]
+
+
+class GradOut(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("d_alpha", "d_sigma_t", "d_g", "d_w")]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsss.so not built at {LIB_PATH}; run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    lib.sss_walk_opts_default.argtypes = [C.POINTER(Opts)]
+    lib.sss_walk_opts_default.restype = None
+    lib.sss_tally_count.argtypes = [C.c_int32, C.c_int32, C.c_int32]
+    lib.sss_tally_count.restype = C.c_int32
+    for f in ("sss_walk_workspace_size", "sss_walk_bwd_workspace_size"):
+        getattr(lib, f).argtypes = [C.POINTER(Params), C.POINTER(Opts)]
+        getattr(lib, f).restype = C.c_size_t
+    lib.sss_walk.argtypes = [C.POINTER(Params), C.POINTER(Opts), C.c_void_p, C.c_size_t,
+                             C.POINTER(Tallies), C.c_void_p]
+    lib.sss_walk.restype = C.c_int
+    lib.sss_walk_bwd.argtypes = [C.POINTER(Params), C.POINTER(Opts), C.c_void_p, C.c_size_t,
+                                 C.POINTER(GradIn), C.POINTER(GradOut), C.c_void_p]
+    lib.sss_walk_bwd.restype = C.c_int
+    lib.sss_read_status.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint32)]
+    lib.sss_read_status.restype = C.c_int
+    lib.sss_philox.argtypes = [C.c_void_p, C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p]
+    lib.sss_philox.restype = C.c_int
+    lib.sss_profile_events.argtypes = [C.c_void_p, C.c_void_p]
+    lib.sss_profile_events.restype = None
+    lib.sss_release_plans.argtypes = []
+    lib.sss_release_plans.restype = None
+    lib.sss_status_string.argtypes = [C.c_int]
+    lib.sss_status_string.restype = C.c_char_p
+    lib.sss_abi_version.argtypes = []
+    lib.sss_abi_version.restype = C.c_int32
+    return lib
+
+
+lib = _load()
+
+
+def _status_string(code: int) -> str:
+    return lib.sss_status_string(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != SSS_OK:
+        raise SSSError(code, what)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class WalkOptions:
+    """Mirror of sss_walk_opts; see include/sss.h for the meaning of each."""
+    nbins: int = 64
+    r_max_mm: float = 10.0
+    mode: int = 0
+    rr_threshold: float = 1.0 / 16.0
+    entry_fresnel: int = 1
+    max_steps: int = 1 << 16
+    seed: int = 0
+    path_offset: int = 0
+    want_sumsq: int = 1
+    schedule: int = 0
+    use_graph: int = 0
+    block_threads: int = 0
+    unit_paths: int = 0
+    regroup: int = 0
+
+    def c(self) -> Opts:
+        return Opts(**asdict(self))
+
+
+@dataclass
+class Media:
+    """Device-side walk inputs (torch CUDA tensors), layouts as in sss_params."""
+    alpha: torch.Tensor         # float32 [K][n]
+    sigma_t: torch.Tensor
+    g: torch.Tensor
+    w: torch.Tensor
+    n_paths: Optional[torch.Tensor] = None    # int32 (as uint32) [n] or None
+    uniform_paths: int = 0
+    thickness_mm: Optional[torch.Tensor] = None
+    n_rel: float = 1.0
+
+    @property
+    def K(self) -> int:
+        return int(self.alpha.shape[0])
+
+    @property
+    def n_inst(self) -> int:
+        return int(self.alpha.shape[1])
+
+    def c(self) -> Params:
+        for t in (self.alpha, self.sigma_t, self.g, self.w):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                    and tuple(t.shape) == (self.K, self.n_inst)):
+                raise ValueError("media arrays must be contiguous float32 CUDA [K][n_inst]")
+        if self.n_paths is not None:
+            assert self.n_paths.is_cuda and self.n_paths.dtype == torch.int32
+            assert self.n_paths.numel() == self.n_inst
+        if self.thickness_mm is not None:
+            assert self.thickness_mm.is_cuda and self.thickness_mm.dtype == torch.float32
+        return Params(_ptr(self.alpha), _ptr(self.sigma_t), _ptr(self.g), _ptr(self.w),
+                      _ptr(self.n_paths), self.uniform_paths, _ptr(self.thickness_mm),
+                      self.n_rel, self.K, self.n_inst)
+
+    @staticmethod
+    def from_inputs(x, device="cuda", per_instance_paths: bool = None) -> "Media":
+        """From a ``paper_2606_27604_b300.inputs.WalkInputs`` (host numpy)."""
+        import numpy as np
+        dev = torch.device(device)
+        f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+        uniform = np.all(x.n_paths == x.n_paths[0]) if per_instance_paths is None \
+            else not per_instance_paths
+        n_paths = None if uniform else torch.from_numpy(
+            x.n_paths.astype(np.uint32).view(np.int32)).to(dev)
+        return Media(f(x.alpha), f(x.sigma_t), f(x.g), f(x.w), n_paths,
+                     int(x.n_paths[0]) if uniform else 0,
+                     None if x.thickness_mm is None else f(x.thickness_mm), float(x.n_rel))
+
+
+def tally_count(nbins: int, K: int, want_sumsq: int) -> int:
+    return lib.sss_tally_count(nbins, K, want_sumsq)
+
+
+def workspace_bytes(m: Media, o: WalkOptions, adjoint: bool = False) -> int:
+    p, oc = m.c(), o.c()
+    f = lib.sss_walk_bwd_workspace_size if adjoint else lib.sss_walk_workspace_size
+    n = f(C.byref(p), C.byref(oc))
+    if n == 0:
+        raise SSSError(1, "workspace size")
+    return n
+
+
+def alloc_workspace(m: Media, o: WalkOptions, adjoint: bool = False) -> torch.Tensor:
+    n = workspace_bytes(m, o, adjoint)
+    return torch.empty(n, dtype=torch.uint8, device=m.alpha.device)
+
+
+def alloc_tallies(m: Media, o: WalkOptions, raw: bool = False) -> dict:
+    n, K, nb = m.n_inst, m.K, o.nbins
+    dev = m.alpha.device
+    d = lambda *s: torch.empty(*s, dtype=torch.float64, device=dev)
+    out = {"R": d(n), "T": d(n), "A": d(n), "bins": d(n, nb), "overflow": d(n),
+           "R_k": d(n, K), "R1": d(n), "steps": d(n),
+           "truncated": torch.empty(n, dtype=torch.int64, device=dev)}
+    if o.want_sumsq:
+        out["stderr_R"] = d(n)
+        out["stderr_bins"] = d(n, nb)
+    if raw:
+        out["raw"] = torch.empty(n, tally_count(nb, K, o.want_sumsq), dtype=torch.int64,
+                                 device=dev)
+    return out
+
+
+def walk(m: Media, o: WalkOptions, workspace: Optional[torch.Tensor] = None,
+         out: Optional[dict] = None, raw: bool = False, stream=None) -> dict:
+    """Forward tallies (sss_walk).  Returns dict of CUDA tensors."""
+    if workspace is None:
+        workspace = alloc_workspace(m, o)
+    if out is None:
+        out = alloc_tallies(m, o, raw)
+    t = Tallies(**{k: _ptr(out.get(k)) for k in
+                   ("R", "T", "A", "bins", "overflow", "R_k", "R1", "stderr_R",
+                    "stderr_bins", "truncated", "steps", "raw")})
+    p, oc = m.c(), o.c()
+    _check(lib.sss_walk(C.byref(p), C.byref(oc), _ptr(workspace), workspace.numel(),
+                        C.byref(t), _stream(stream)), "sss_walk")
+    out["_workspace"] = workspace
+    return out
+
+
+def walk_bwd(m: Media, o: WalkOptions, grad_R=None, grad_bins=None, grad_R_k=None,
+             grad_T=None, workspace: Optional[torch.Tensor] = None, out: Optional[dict] = None,
+             stream=None) -> dict:
+    """Path-replay adjoint (sss_walk_bwd): d(sum upstream * tallies)/d(media)."""
+    if workspace is None:
+        workspace = alloc_workspace(m, o, adjoint=True)
+    dev = m.alpha.device
+    if out is None:
+        out = {k: torch.empty(m.K, m.n_inst, dtype=torch.float64, device=dev)
+               for k in ("d_alpha", "d_sigma_t", "d_g", "d_w")}
+    for g in (grad_R, grad_bins, grad_R_k, grad_T):
+        if g is not None:
+            assert g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()
+    gi = GradIn(_ptr(grad_R), _ptr(grad_bins), _ptr(grad_R_k), _ptr(grad_T))
+    go = GradOut(*(_ptr(out.get(k)) for k in ("d_alpha", "d_sigma_t", "d_g", "d_w")))
+    p, oc = m.c(), o.c()
+    _check(lib.sss_walk_bwd(C.byref(p), C.byref(oc), _ptr(workspace), workspace.numel(),
+                            C.byref(gi), C.byref(go), _stream(stream)), "sss_walk_bwd")
+    out["_workspace"] = workspace
+    return out
+
+
+def read_status(workspace: torch.Tensor, stream=None):
+    """(status code, flag bits) left in the workspace by the last call."""
+    flags = C.c_uint32(0)
+    code = lib.sss_read_status(_ptr(workspace), _stream(stream), C.byref(flags))
+    return code, flags.value
+
+
+def philox(ctr: torch.Tensor, key: int, stream=None) -> torch.Tensor:
+    """Device Philox4x32-10 blocks for int32 counters [n][4] (bit patterns)."""
+    assert ctr.is_cuda and ctr.dtype == torch.int32 and ctr.shape[-1] == 4
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    _check(lib.sss_philox(_ptr(ctr), key, ctr.shape[0], _ptr(out), _stream(stream)), "sss_philox")
+    return out
+
+
+def profile_events(start=None, stop=None):
+    """Record torch.cuda.Event pair around the main walk kernel of the next
+    calls from this thread (None, None to stop)."""
+    if start is None or stop is None:
+        lib.sss_profile_events(None, None)
+    else:
+        lib.sss_profile_events(C.c_void_p(start.cuda_event), C.c_void_p(stop.cuda_event))
+
+
+def release_plans():
+    lib.sss_release_plans()
+
+
+def abi_version() -> int:
+    return lib.sss_abi_version()
+
+
+class SSSWalk(torch.autograd.Function):
+    """Differentiable forward walk: (alpha, sigma_t, g, w) -> (R, bins, R_k).
+
+    backward runs the path-replay adjoint with the same options and seed."""
+
+    @staticmethod
+    def forward(ctx, alpha, sigma_t, g, w, template: Media, o: WalkOptions):
+        m = Media(alpha.detach().contiguous(), sigma_t.detach().contiguous(),
+                  g.detach().contiguous(), w.detach().contiguous(), template.n_paths,
+                  template.uniform_paths, template.thickness_mm, template.n_rel)
+        r = walk(m, o)
+        ctx.m, ctx.o = m, o
+        return r["R"], r["bins"], r["R_k"]
+
+    @staticmethod
+    def backward(ctx, gR, gB, gK):
+        f = lambda t: None if t is None else t.detach().to(torch.float64).contiguous()
+        d = walk_bwd(ctx.m, ctx.o, grad_R=f(gR), grad_bins=f(gB), grad_R_k=f(gK))
+        cast = lambda t: t.to(torch.float32)
+        return cast(d["d_alpha"]), cast(d["d_sigma_t"]), cast(d["d_g"]), cast(d["d_w"]), \
+            None, None

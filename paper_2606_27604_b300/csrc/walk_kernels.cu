@@ -1,0 +1,545 @@
+// walk_kernels.cu -- device kernels of the mixture-of-media random walk.
+//
+//   validate_params   : one thread per instance; flags out-of-range media.
+//   units_count/scan  : per-instance work-unit counts -> exclusive prefix
+//                       (uneven path budgets only).
+//   walk_persistent<ADJ> : persistent batched walk.  Each warp takes work
+//                       units (instance, range of paths) from a global
+//                       counter; its lanes each run one path and, as soon as
+//                       enough lanes are idle, are refilled from the warp's
+//                       current unit (path regrouping).  A warp holds two
+//                       units at once (double-buffered slots) so the tail of
+//                       one unit overlaps the start of the next.  Tallies are
+//                       64-bit fixed point (weight * 2^32), summed with
+//                       shared-memory atomics per slot and flushed with one
+//                       global atomic per nonzero entry when a unit is done:
+//                       integer sums do not depend on order, so a rerun is
+//                       bit-identical whatever the launch shape.
+//                       ADJ = true is the path-replay adjoint: it re-runs
+//                       the same paths and accumulates score-weighted
+//                       upstream derivatives instead of tallies.
+//   walk_plain        : baseline: one thread per path of one instance.
+//   finalize_*        : fixed point -> float64 means / standard errors.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "walk_core.cuh"
+#include "walk_kernels.cuh"
+
+namespace sss {
+
+static constexpr float kFix = 4294967296.0f;  // 2^32
+static constexpr double kInvFix = 1.0 / 4294967296.0;
+static constexpr unsigned kFull = 0xffffffffu;
+
+// -------------------------------------------------------------- validate --
+__global__ void validate_params_kernel(WalkConst c, unsigned int* status) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.n_inst) return;
+  bool bad = false;
+  float wsum = 0.0f;
+  for (int k = 0; k < c.K; ++k) {
+    const size_t o = (size_t)k * c.n_inst + i;
+    const float a = c.alpha[o], s = c.sigma_t[o], g = c.g[o], w = c.w[o];
+    bad |= !(a >= 0.0f && a <= 1.0f);
+    bad |= !(s > 0.0f && s < __int_as_float(0x7f800000));
+    bad |= !(g > -1.0f && g < 1.0f);
+    bad |= !(w >= 0.0f && w <= 1.0f + 1e-5f);
+    wsum += w;
+  }
+  bad |= !(fabsf(wsum - 1.0f) <= 1e-5f);
+  if (c.thickness) {
+    const float d = c.thickness[i];
+    bad |= !(d > 0.0f);  // +inf allowed, NaN and <= 0 rejected
+  }
+  if (bad) atomicOr(status, SSS_DEV_FLAG_PARAM);
+}
+
+// -------------------------------------------------------- unit prefix sum --
+// counts[i] = ceil(N_i / C); prefix[i] = sum_{j<i} counts[j]; prefix[n] = total.
+// Three passes: per-block sums, one-block scan of the block sums, fix-up.
+__global__ void unit_block_sums_kernel(const uint32_t* n_paths, uint32_t n, uint32_t C,
+                                       unsigned long long* block_sums) {
+  __shared__ unsigned long long red[32];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long v = i < n ? (unsigned long long)((n_paths[i] + (uint64_t)C - 1) / C) : 0ull;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = v;
+  }
+}
+
+__global__ void unit_scan_block_sums_kernel(unsigned long long* block_sums, uint32_t nblocks,
+                                            unsigned long long* total) {
+  // single block of 1024 threads; sequential over chunks of 1024
+  __shared__ unsigned long long buf[1024];
+  unsigned long long carry = 0;
+  for (uint32_t base = 0; base < nblocks; base += 1024) {
+    const uint32_t i = base + threadIdx.x;
+    buf[threadIdx.x] = i < nblocks ? block_sums[i] : 0ull;
+    __syncthreads();
+    // Hillis-Steele inclusive scan
+    for (int o = 1; o < 1024; o <<= 1) {
+      unsigned long long t = threadIdx.x >= (unsigned)o ? buf[threadIdx.x - o] : 0ull;
+      __syncthreads();
+      buf[threadIdx.x] += t;
+      __syncthreads();
+    }
+    const unsigned long long incl = buf[threadIdx.x];
+    const unsigned long long excl = incl - (i < nblocks ? block_sums[i] : 0ull);
+    __syncthreads();
+    if (i < nblocks) block_sums[i] = carry + excl;
+    carry += buf[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void unit_prefix_kernel(const uint32_t* n_paths, uint32_t n, uint32_t C,
+                                   const unsigned long long* block_offsets,
+                                   const unsigned long long* total,
+                                   unsigned long long* prefix) {
+  __shared__ unsigned long long warp_tot[32];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned long long v =
+      i < n ? (unsigned long long)((n_paths[i] + (uint64_t)C - 1) / C) : 0ull;
+  unsigned long long incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0ull;
+    unsigned long long ti = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(kFull, ti, o);
+      if (lane >= o) ti += u;
+    }
+    warp_tot[lane] = ti - t;  // exclusive
+  }
+  __syncthreads();
+  if (i < n) prefix[i] = block_offsets[blockIdx.x] + warp_tot[wid] + incl - v;
+  if (i == 0) prefix[n] = *total;
+}
+
+// ------------------------------------------------------------- persistent --
+struct UnitRange {
+  uint32_t inst, p0, p1;
+  bool ok;
+};
+
+__device__ __forceinline__ UnitRange unit_lookup(const WalkSched& s, const WalkConst& c,
+                                                 unsigned long long u) {
+  UnitRange r;
+  r.ok = s.prefix == nullptr ? u < s.total_units : u < s.prefix[c.n_inst];
+  if (!r.ok) return r;
+  uint32_t inst;
+  unsigned long long first;
+  if (s.prefix == nullptr) {
+    inst = (uint32_t)(u / s.units_per_inst);
+    first = (unsigned long long)inst * s.units_per_inst;
+  } else {
+    // largest i with prefix[i] <= u (instances with no units are skipped)
+    uint32_t lo = 0, hi = c.n_inst;  // prefix[lo] <= u < prefix[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = lo + ((hi - lo) >> 1);
+      if (s.prefix[mid] <= u) lo = mid;
+      else hi = mid;
+    }
+    inst = lo;
+    first = s.prefix[lo];
+  }
+  const uint32_t N = c.n_paths ? c.n_paths[inst] : c.uniform_paths;
+  const unsigned long long chunk = u - first;
+  r.inst = inst;
+  r.p0 = (uint32_t)(chunk * s.unit_paths);
+  const unsigned long long e = (chunk + 1) * s.unit_paths;
+  r.p1 = e < N ? (uint32_t)e : N;
+  return r;
+}
+
+// Upstream-derivative scale of one instance for the adjoint: a power of two
+// 2^E chosen so that |weight * upstream * score| < 2^20 * max|upstream| per
+// path cannot overflow an int64 sum over N paths.
+__device__ __forceinline__ int grad_exponent(const WalkConst& c, const GradIn& gi, uint32_t inst,
+                                             int lane) {
+  double vmax = 0.0;
+  if (gi.grad_bins) {
+    for (int b = lane; b < c.nbins; b += 32)
+      vmax = fmax(vmax, fabs(gi.grad_bins[(size_t)inst * c.nbins + b]));
+  }
+  for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(kFull, vmax, o));
+  double vk = 0.0;
+  if (gi.grad_R_k)
+    for (int k = 0; k < c.K; ++k) vk = fmax(vk, fabs(gi.grad_R_k[(size_t)inst * c.K + k]));
+  double top = vmax + vk + (gi.grad_R ? fabs(gi.grad_R[inst]) : 0.0);
+  double bot = gi.grad_T ? fabs(gi.grad_T[inst]) : 0.0;
+  const double v = fmax(top, bot);
+  if (!(v > 0.0)) return 0;
+  const uint32_t N = c.n_paths ? c.n_paths[inst] : c.uniform_paths;
+  const int lgN = N > 1 ? 32 - __clz(N - 1) : 0;
+  int ev;
+  frexp(v, &ev);  // v < 2^ev
+  int E = 62 - 20 - lgN - ev;
+  E = max(-100, min(100, E));
+  return E;
+}
+
+template <bool ADJ>
+__global__ void __launch_bounds__(256)
+walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
+  extern __shared__ unsigned long long smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int slot_words = s.slot_words;
+  unsigned long long* slot_mem = smem + (size_t)wib * 2 * slot_words;
+  for (int j = lane; j < 2 * slot_words; j += 32) slot_mem[j] = 0ull;
+  __syncwarp();
+
+  // Warp-uniform slot state.
+  uint32_t s_inst[2] = {0u, 0u}, s_next[2] = {0u, 0u}, s_end[2] = {0u, 0u};
+  float s_d[2] = {0.0f, 0.0f};
+  float s_scale[2] = {1.0f, 1.0f};   // adjoint fixed-point scale
+  float s_lim[2] = {0.0f, 0.0f};     // adjoint per-path magnitude limit
+  float s_wsum[2] = {1.0f, 1.0f};
+  bool s_live[2] = {false, false};
+  int cur = 0;
+  bool more = true;
+
+  // Lane state.
+  bool valid = false;
+  int myslot = 0;
+  Path p;
+  p.step = 0;
+
+  auto fetch = [&](int o) -> bool {
+    unsigned long long u = 0;
+    if (lane == 0) u = atomicAdd(s.unit_counter, 1ull);
+    u = __shfl_sync(kFull, u, 0);
+    const UnitRange r = unit_lookup(s, c, u);
+    if (!r.ok) return false;
+    s_inst[o] = r.inst;
+    s_next[o] = r.p0;
+    s_end[o] = r.p1;
+    s_d[o] = c.thickness ? __ldg(c.thickness + r.inst) : __int_as_float(0x7f800000);
+    s_live[o] = true;
+    if (ADJ) {
+      const int E = grad_exponent(c, gi, r.inst, lane);
+      s_scale[o] = ldexpf(1.0f, E);
+      const uint32_t N = c.n_paths ? c.n_paths[r.inst] : c.uniform_paths;
+      const int lgN = N > 1 ? 32 - __clz(N - 1) : 0;
+      s_lim[o] = ldexpf(1.0f, 62 - lgN);
+      float ws = 0.0f;
+      for (int k = 0; k < c.K; ++k) ws = __fadd_rn(ws, __ldg(c.w + (size_t)k * c.n_inst + r.inst));
+      s_wsum[o] = ws;
+    }
+    return true;
+  };
+
+  auto flush = [&](int o) {
+    __syncwarp();
+    unsigned long long* m = slot_mem + (size_t)o * slot_words;
+    unsigned long long* dst = ADJ ? t.raw : t.raw + (size_t)s_inst[o] * slot_words;
+    for (int j = lane; j < slot_words; j += 32) {
+      const unsigned long long v = m[j];
+      if (v != 0ull) {
+        if (ADJ) {
+          // layout [4][K][n_inst]
+          atomicAdd(dst + (size_t)j * c.n_inst + s_inst[o], v);
+        } else {
+          atomicAdd(dst + j, v);
+        }
+        m[j] = 0ull;
+      }
+    }
+    __syncwarp();
+    s_live[o] = false;
+  };
+
+  if (!fetch(0)) more = false;
+
+  while (true) {
+    // ---------------- refill idle lanes (path regrouping) ----------------
+    unsigned idle = __ballot_sync(kFull, !valid);
+    const int n_idle = __popc(idle);
+    if (n_idle >= s.regroup || n_idle == 32) {
+      while (idle != 0u) {
+        if (s_next[cur] < s_end[cur]) {
+          const uint32_t avail = s_end[cur] - s_next[cur];
+          const uint32_t take = min((uint32_t)__popc(idle), avail);
+          const int rank = __popc(idle & ((1u << lane) - 1u));
+          if (!valid && (uint32_t)rank < take) {
+            path_init(c, s_inst[cur], c.path_offset + s_next[cur] + rank, s_d[cur], p);
+            valid = true;
+            myslot = cur;
+          }
+          s_next[cur] += take;
+          idle = __ballot_sync(kFull, !valid);
+        } else {
+          if (!more) break;
+          const int o = cur ^ 1;
+          if (s_live[o]) {
+            if (__ballot_sync(kFull, valid && myslot == o) != 0u) break;  // still running
+            flush(o);
+          }
+          if (!fetch(o)) {
+            more = false;
+            break;
+          }
+          cur = o;
+        }
+      }
+    }
+    if (__ballot_sync(kFull, valid) == 0u) {
+      if (!more && s_next[cur] >= s_end[cur]) break;
+      continue;
+    }
+
+    // ---------------- advance every live path by `burst` draws -----------
+    for (int it = 0; it < s.burst; ++it) {
+      if (valid) {
+        const int ev = path_step<ADJ>(c, p);
+        if (ev != EV_CONTINUE) {
+          unsigned long long* m = slot_mem + (size_t)myslot * slot_words;
+          if (!ADJ) {
+            const int nb = c.nbins;
+            if (ev == EV_TOP) {
+              const unsigned long long q = __float2ull_rn(__fmul_rn(p.W, kFix));
+              atomicAdd(m + p.bin, q);
+              atomicAdd(m + nb + 1 + p.k, q);
+              if (p.n_coll == 1u) atomicAdd(m + nb + 1 + c.K, q);
+              if (s.want_sumsq)
+                atomicAdd(m + nb + 6 + c.K + p.bin,
+                          __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
+            } else if (ev == EV_BOTTOM) {
+              atomicAdd(m + nb + 2 + c.K, __float2ull_rn(__fmul_rn(p.W, kFix)));
+            } else if (ev == EV_TRUNC) {
+              atomicAdd(m + nb + 4 + c.K, 1ull);
+            }
+            if (p.Aacc > 0.0f) atomicAdd(m + nb + 3 + c.K, __float2ull_rn(__fmul_rn(p.Aacc, kFix)));
+            atomicAdd(m + nb + 5 + c.K, (unsigned long long)p.step);
+          } else {
+            float v = 0.0f;
+            if (ev == EV_TOP) {
+              double vd = 0.0;
+              if (gi.grad_R) vd += gi.grad_R[p.inst];
+              if (gi.grad_bins && p.bin < c.nbins) vd += gi.grad_bins[(size_t)p.inst * c.nbins + p.bin];
+              if (gi.grad_R_k) vd += gi.grad_R_k[(size_t)p.inst * c.K + p.k];
+              v = (float)vd;
+            } else if (ev == EV_BOTTOM) {
+              if (gi.grad_T) v = (float)gi.grad_T[p.inst];
+            }
+            if (v != 0.0f) {
+              const float sc = s_scale[myslot];
+              const float lim = s_lim[myslot];
+              const float Wv = __fmul_rn(__fmul_rn(p.W, v), sc);
+              const float nf = (float)p.n_coll;
+              float q[4];
+              q[0] = __fmul_rn(Wv, __fdiv_rn(nf, p.alpha));
+              q[1] = __fmul_rn(Wv, __fsub_rn(__fmul_rn(nf, p.inv_sigt), p.L));
+              q[2] = __fmul_rn(Wv, p.G);
+              q[3] = __fmul_rn(Wv, __fdiv_rn(s_wsum[myslot], c.w[(size_t)p.k * c.n_inst + p.inst]));
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                float x = q[j];
+                if (!(fabsf(x) < lim)) {
+                  atomicOr(s.status, SSS_DEV_FLAG_OVERFLOW);
+                  x = (x != x) ? 0.0f : copysignf(lim, x);
+                }
+                atomicAdd(m + j * c.K + p.k, (unsigned long long)__float2ll_rn(x));
+              }
+            }
+          }
+          if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
+          valid = false;
+        }
+      }
+    }
+  }
+  // flush whatever is still held
+  for (int o = 0; o < 2; ++o)
+    if (s_live[o]) flush(o);
+}
+
+// ------------------------------------------------------------------ plain --
+// One thread per path of a single instance; block-level shared tallies.
+__global__ void __launch_bounds__(256)
+walk_plain_kernel(WalkConst c, WalkSched s, TallyOut t, uint32_t inst, uint32_t N) {
+  extern __shared__ unsigned long long smem[];
+  const int slot_words = s.slot_words;
+  for (int j = threadIdx.x; j < slot_words; j += blockDim.x) smem[j] = 0ull;
+  __syncthreads();
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < N) {
+    Path p;
+    const float d = c.thickness ? c.thickness[inst] : __int_as_float(0x7f800000);
+    path_init(c, inst, c.path_offset + j, d, p);
+    int ev;
+    do {
+      ev = path_step<false>(c, p);
+    } while (ev == EV_CONTINUE);
+    const int nb = c.nbins;
+    if (ev == EV_TOP) {
+      const unsigned long long q = __float2ull_rn(__fmul_rn(p.W, kFix));
+      atomicAdd(smem + p.bin, q);
+      atomicAdd(smem + nb + 1 + p.k, q);
+      if (p.n_coll == 1u) atomicAdd(smem + nb + 1 + c.K, q);
+      if (s.want_sumsq)
+        atomicAdd(smem + nb + 6 + c.K + p.bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
+    } else if (ev == EV_BOTTOM) {
+      atomicAdd(smem + nb + 2 + c.K, __float2ull_rn(__fmul_rn(p.W, kFix)));
+    } else if (ev == EV_TRUNC) {
+      atomicAdd(smem + nb + 4 + c.K, 1ull);
+      atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
+    }
+    if (p.Aacc > 0.0f) atomicAdd(smem + nb + 3 + c.K, __float2ull_rn(__fmul_rn(p.Aacc, kFix)));
+    atomicAdd(smem + nb + 5 + c.K, (unsigned long long)p.step);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < slot_words; k += blockDim.x) {
+    const unsigned long long v = smem[k];
+    if (v) atomicAdd(t.raw + (size_t)inst * slot_words + k, v);
+  }
+}
+
+// --------------------------------------------------------------- finalize --
+__device__ __forceinline__ double se_of(double s, double s2, double n) {
+  if (n < 2.0) return 0.0;
+  const double m = s / n;
+  const double v = (s2 / n - m * m) * n / (n - 1.0);
+  return v > 0.0 ? sqrt(v / n) : 0.0;
+}
+
+__global__ void finalize_tallies_kernel(WalkConst c, WalkSched s, TallyOut t) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.n_inst) return;
+  const int nb = c.nbins, K = c.K, nt = s.slot_words;
+  const unsigned long long* r = t.raw + (size_t)i * nt;
+  const uint32_t N = c.n_paths ? c.n_paths[i] : c.uniform_paths;
+  const double n = (double)N;
+  const double inv = N ? kInvFix / n : 0.0;
+  unsigned long long sR = 0, s2R = 0;
+  for (int b = 0; b <= nb; ++b) {
+    sR += r[b];
+    if (s.want_sumsq) s2R += r[nb + 6 + K + b];
+  }
+  if (t.R) t.R[i] = (double)sR * inv;
+  if (t.bins)
+    for (int b = 0; b < nb; ++b) t.bins[(size_t)i * nb + b] = (double)r[b] * inv;
+  if (t.overflow) t.overflow[i] = (double)r[nb] * inv;
+  if (t.R_k)
+    for (int k = 0; k < K; ++k) t.R_k[(size_t)i * K + k] = (double)r[nb + 1 + k] * inv;
+  if (t.R1) t.R1[i] = (double)r[nb + 1 + K] * inv;
+  if (t.T) t.T[i] = (double)r[nb + 2 + K] * inv;
+  if (t.A) t.A[i] = (double)r[nb + 3 + K] * inv;
+  if (t.truncated) t.truncated[i] = r[nb + 4 + K];
+  if (t.steps) t.steps[i] = N ? (double)r[nb + 5 + K] / n : 0.0;
+  if (s.want_sumsq && N) {
+    if (t.stderr_R) t.stderr_R[i] = se_of((double)sR * kInvFix, (double)s2R * kInvFix, n);
+    if (t.stderr_bins)
+      for (int b = 0; b < nb; ++b)
+        t.stderr_bins[(size_t)i * nb + b] =
+            se_of((double)r[b] * kInvFix, (double)r[nb + 6 + K + b] * kInvFix, n);
+  }
+  if (t.raw_out)
+    for (int j = 0; j < nt; ++j) t.raw_out[(size_t)i * nt + j] = r[j];
+}
+
+__global__ void finalize_grads_kernel(WalkConst c, GradIn gi, const unsigned long long* raw,
+                                      GradOut go) {
+  // one warp per instance (grad_exponent reduces over the bins with shuffles)
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= c.n_inst) return;
+  const int E = grad_exponent(c, gi, i, lane);
+  if (lane != 0) return;
+  const uint32_t N = c.n_paths ? c.n_paths[i] : c.uniform_paths;
+  const double scale = N ? ldexp(1.0, -E) / (double)N : 0.0;
+  double* outs[4] = {go.d_alpha, go.d_sigma_t, go.d_g, go.d_w};
+  for (int q = 0; q < 4; ++q) {
+    if (!outs[q]) continue;
+    for (int k = 0; k < c.K; ++k) {
+      const size_t o = (size_t)(q * c.K + k) * c.n_inst + i;
+      outs[q][(size_t)k * c.n_inst + i] = (double)(long long)raw[o] * scale;
+    }
+  }
+  if (go.d_w) {
+    for (int k = 0; k < c.K; ++k)
+      if (c.w[(size_t)k * c.n_inst + i] == 0.0f) atomicOr(go.status, SSS_DEV_FLAG_ZERO_WEIGHT);
+  }
+}
+
+// ------------------------------------------------------------ diagnostics --
+__global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n,
+                              uint32_t* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint4 r = philox4x32_10(c, k0, k1);
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+// ---------------------------------------------------------------- launch --
+void launch_validate(const WalkConst& c, unsigned int* status, cudaStream_t st) {
+  if (c.n_inst == 0) return;
+  validate_params_kernel<<<(c.n_inst + 255) / 256, 256, 0, st>>>(c, status);
+}
+
+void launch_unit_prefix(const uint32_t* n_paths, uint32_t n, uint32_t C,
+                        unsigned long long* block_sums, unsigned long long* total,
+                        unsigned long long* prefix, cudaStream_t st) {
+  const uint32_t nb = (n + 255) / 256;
+  if (n > 0) unit_block_sums_kernel<<<nb, 256, 0, st>>>(n_paths, n, C, block_sums);
+  unit_scan_block_sums_kernel<<<1, 1024, 0, st>>>(block_sums, nb, total);
+  if (n > 0) unit_prefix_kernel<<<nb, 256, 0, st>>>(n_paths, n, C, block_sums, total, prefix);
+  else cudaMemcpyAsync(prefix, total, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+}
+
+void launch_walk_persistent(bool adj, int grid, int block, size_t smem, const WalkConst& c,
+                            const WalkSched& s, const TallyOut& t, const GradIn& gi,
+                            cudaStream_t st) {
+  if (adj) walk_persistent_kernel<true><<<grid, block, smem, st>>>(c, s, t, gi);
+  else walk_persistent_kernel<false><<<grid, block, smem, st>>>(c, s, t, gi);
+}
+
+const void* persistent_kernel_ptr(bool adj) {
+  return adj ? (const void*)walk_persistent_kernel<true>
+             : (const void*)walk_persistent_kernel<false>;
+}
+
+void launch_walk_plain(const WalkConst& c, const WalkSched& s, const TallyOut& t, uint32_t inst,
+                       uint32_t N, cudaStream_t st) {
+  if (N == 0) return;
+  walk_plain_kernel<<<(N + 255) / 256, 256, (size_t)s.slot_words * 8, st>>>(c, s, t, inst, N);
+}
+
+void launch_finalize_tallies(const WalkConst& c, const WalkSched& s, const TallyOut& t,
+                             cudaStream_t st) {
+  if (c.n_inst == 0) return;
+  finalize_tallies_kernel<<<(c.n_inst + 127) / 128, 128, 0, st>>>(c, s, t);
+}
+
+void launch_finalize_grads(const WalkConst& c, const GradIn& gi, const unsigned long long* raw,
+                           const GradOut& go, cudaStream_t st) {
+  if (c.n_inst == 0) return;
+  const uint64_t threads = (uint64_t)c.n_inst * 32;
+  finalize_grads_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(c, gi, raw, go);
+}
+
+void launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
+                   cudaStream_t st) {
+  if (n <= 0) return;
+  philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctr, k0, k1, n, out);
+}
+
+}  // namespace sss

@@ -1,0 +1,241 @@
+"""GPU forward walk vs the FP64 oracle, through the C ABI.
+
+Both sides walk the same Philox4x32-10 streams (each implements the
+generator from its published definition), so tallies agree far inside the
+statistical error; the tests check that tight same-stream bound, the
+statistical bar (4 standard errors), closed forms, determinism and edge
+cases.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import hfunction as hf
+from paper_2606_27604_b300 import inputs
+from gpu_helpers import (run_gpu, run_oracle, compare_same_stream, compare_sigma,
+                         to_oracle_opts, TALLIES)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_27604_b300 import api as a
+    return a
+
+
+def opts(api, **kw):
+    o = api.WalkOptions()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+# ------------------------------------------------------------------ Philox --
+def test_device_philox_matches_oracle(api):
+    import torch
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    ctr[2] = (65535, 2 ** 27 - 1, 84934655, 1)
+    for key in (0, 1000, 0x123456789ABCDEF0):
+        got = api.philox(torch.from_numpy(ctr.view(np.int32)).cuda(), key).cpu().numpy()
+        got = got.view(np.uint32)
+        kk = (key & 0xFFFFFFFF, key >> 32)
+        ref = np.array([oracle.philox4x32_10(c, kk) for c in ctr[:512]])
+        np.testing.assert_array_equal(got[:512], ref)
+
+
+# ------------------------------------------------- single wavelength sets --
+def test_single_wavelength_parity_and_closed_forms(api):
+    x = inputs.single_wavelength(param_seed=0, n_paths=1 << 18)
+    o = opts(api, nbins=32, r_max_mm=10.0, seed=1000)
+    g, code, flags = run_gpu(x, o)
+    assert code == 0 and flags == 0
+    r = run_oracle(x, o)
+    worst, where = compare_same_stream(g, r, x.n_paths, r["steps"])
+    print("same-stream worst ratio", worst, where)
+    assert worst <= 1.0, where
+    assert not compare_sigma(g, r, keys=("R", "bins", "R1", "T", "A", "overflow"))
+    # closed forms for the isotropic index-matched sets
+    for i, a in enumerate(inputs.ALPHA_SET0):
+        Rc, R1c = hf.reflectance_total(a), hf.reflectance_single(a)
+        assert abs(g["R"][i] - Rc) <= 4 * g["stderr_R"][i]
+        assert abs(g["R1"][i] - R1c) <= 4 * r["se_R1"][i]
+    np.testing.assert_allclose(g["stderr_R"], r["se_R"], rtol=2e-2)
+    assert np.all(g["truncated"] == 0)
+
+
+def test_h_function_at_1e8_paths(api):
+    # 2^27 paths per set: relative error <= 1e-3 and within 4 standard errors
+    x = inputs.single_wavelength(param_seed=0, n_paths=1 << 27).subset(np.arange(10))
+    o = opts(api, nbins=32, r_max_mm=10.0, seed=1000)
+    g, code, flags = run_gpu(x, o)
+    assert code == 0
+    for i, a in enumerate(inputs.ALPHA_SET0):
+        Rc, R1c = hf.reflectance_total(a), hf.reflectance_single(a)
+        rel = abs(g["R"][i] - Rc) / Rc
+        print(f"alpha={a}: R={g['R'][i]:.7f} closed={Rc:.7f} rel={rel:.2e} "
+              f"z={(g['R'][i]-Rc)/g['stderr_R'][i]:.2f}")
+        assert rel <= 1e-3
+        assert abs(g["R"][i] - Rc) <= 4 * g["stderr_R"][i]
+        assert abs(g["R1"][i] - R1c) / R1c <= 1e-3
+
+
+# ------------------------------------------------------- spectral field ---
+def test_spectral_field_small_parity(api):
+    # a few texels x 81 bands, several units per instance and a ragged tail
+    x = inputs.spectral_field(n_texels=6, param_seed=1, n_paths=5000)
+    o = opts(api, nbins=64, r_max_mm=10.0, seed=1001, unit_paths=1024)
+    g, code, flags = run_gpu(x, o)
+    assert code == 0 and flags == 0
+    r = run_oracle(x, o)
+    worst, where = compare_same_stream(g, r, x.n_paths, r["steps"])
+    print("same-stream worst ratio", worst, where)
+    assert worst <= 1.0, where
+    assert not compare_sigma(g, r, keys=("R", "bins", "R1", "A", "overflow"))
+
+
+def test_spectral_field_full_size_sampled(api):
+    # 256 x 256 texels x 81 bands at 4096 paths, as the benchmark runs it;
+    # the oracle re-walks a sample of instances under their instance numbers.
+    x = inputs.spectral_field(n_texels=256 * 256, param_seed=1, n_paths=4096)
+    o = opts(api, nbins=64, r_max_mm=10.0, seed=1001)
+    g, code, flags = run_gpu(x, o)
+    assert code == 0 and flags == 0
+    n = x.n_inst
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 60)]))
+    xs = x.subset(idx)
+    r = run_oracle(xs, o, inst_ids=idx)
+    gs = {k: g[k][idx] for k in TALLIES}
+    worst, where = compare_same_stream(gs, r, xs.n_paths, r["steps"])
+    print("same-stream worst ratio", worst, where)
+    assert worst <= 1.0, where
+    # properties of every instance
+    W0 = 1.0 - ((1.4 - 1) / 2.4) ** 2
+    np.testing.assert_allclose(g["R"], g["bins"].sum(1) + g["overflow"], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(g["R"], g["R_k"].sum(1), rtol=1e-12, atol=0)
+    assert np.all(g["bins"] >= 0) and np.all(g["R"] <= W0)
+    assert np.all(np.isfinite(g["R"])) and np.all(g["truncated"] == 0)
+    assert np.all(g["T"] == 0)   # semi-infinite
+
+
+def test_uneven_batch_sampled(api):
+    x = inputs.uneven_batch(n_inst=4096, param_seed=2)
+    o = opts(api, nbins=64, r_max_mm=10.0, seed=1002)
+    g, code, flags = run_gpu(x, o)
+    assert code == 0 and flags == 0
+    order = np.argsort(x.n_paths)
+    idx = np.sort(np.concatenate([order[:40], order[-2:],
+                                  np.random.default_rng(1).choice(order[40:-2], 8, False)]))
+    xs = x.subset(idx)
+    r = run_oracle(xs, o, inst_ids=idx)
+    gs = {k: g[k][idx] for k in TALLIES}
+    worst, where = compare_same_stream(gs, r, xs.n_paths, r["steps"])
+    print("same-stream worst ratio", worst, where)
+    assert worst <= 1.0, where
+    np.testing.assert_allclose(g["R"], g["bins"].sum(1) + g["overflow"], rtol=1e-12)
+    fin = np.isfinite(x.thickness_mm)
+    assert np.all(g["T"][~fin] == 0) and np.any(g["T"][fin] > 0)
+
+
+# ------------------------------------------------------------ determinism --
+def test_rerun_and_launch_shapes_are_bit_exact(api):
+    x = inputs.uneven_batch(n_inst=300, param_seed=7, log2_min=8, log2_max=14)
+    base = opts(api, nbins=48, r_max_mm=6.0, seed=77)
+    ref, code, _ = run_gpu(x, base, raw=True)
+    assert code == 0
+    again, _, _ = run_gpu(x, base, raw=True)
+    np.testing.assert_array_equal(ref["raw"], again["raw"])
+    for kw in ({"block_threads": 128}, {"block_threads": 64, "unit_paths": 96},
+               {"unit_paths": 4096, "regroup": 1}, {"regroup": 32}, {"unit_paths": 33},
+               {"use_graph": 1}, {"schedule": 1}):
+        o = opts(api, nbins=48, r_max_mm=6.0, seed=77, **kw)
+        got, code, _ = run_gpu(x, o, raw=True)
+        assert code == 0
+        np.testing.assert_array_equal(ref["raw"], got["raw"], err_msg=str(kw))
+    # graph replay of the cached plan
+    o = opts(api, nbins=48, r_max_mm=6.0, seed=77, use_graph=1)
+    got, _, _ = run_gpu(x, o, raw=True)
+    np.testing.assert_array_equal(ref["raw"], got["raw"])
+    api.release_plans()
+
+
+def test_split_path_ranges_add_up_exactly(api):
+    import torch
+    x = inputs.spectral_field(n_texels=2, param_seed=3, n_paths=3000)
+    full, _, _ = run_gpu(x, opts(api, seed=5), raw=True)
+    a = x.subset(np.arange(x.n_inst)); a.n_paths = np.full(x.n_inst, 1234, np.uint32)
+    b = x.subset(np.arange(x.n_inst)); b.n_paths = np.full(x.n_inst, 3000 - 1234, np.uint32)
+    ra, _, _ = run_gpu(a, opts(api, seed=5), raw=True)
+    rb, _, _ = run_gpu(b, opts(api, seed=5, path_offset=1234), raw=True)
+    np.testing.assert_array_equal(full["raw"], ra["raw"] + rb["raw"])
+
+
+def test_three_identical_media_equal_one(api):
+    x = inputs.spectral_field(n_texels=3, param_seed=4, n_paths=4000)
+    x3 = x.subset(np.arange(x.n_inst))
+    for name in ("alpha", "sigma_t", "g"):
+        arr = getattr(x3, name)
+        arr[1] = arr[0]; arr[2] = arr[0]
+    x1 = x3.subset(np.arange(x.n_inst))
+    x1.alpha, x1.sigma_t, x1.g = x3.alpha[:1].copy(), x3.sigma_t[:1].copy(), x3.g[:1].copy()
+    x1.w = np.ones((1, x.n_inst), np.float32)
+    o = opts(api, seed=9)
+    g3, _, _ = run_gpu(x3, o)
+    g1, _, _ = run_gpu(x1, o)
+    for k in ("R", "T", "A", "bins", "overflow", "R1"):
+        np.testing.assert_array_equal(g3[k], g1[k], err_msg=k)
+
+
+# ----------------------------------------------------------------- edges --
+def test_edge_cases(api):
+    import torch
+    # empty batch
+    x = inputs.single_wavelength(n_paths=64).subset(np.arange(0))
+    g, code, _ = run_gpu(x, opts(api, nbins=8))
+    assert code == 0 and g["R"].shape == (0,)
+    # zero and one path budgets, one bin, maximum bins
+    x = inputs.uneven_batch(n_inst=5, param_seed=9)
+    x.n_paths = np.array([0, 1, 7, 0, 1000], np.uint32)
+    for nb in (1, 1024):
+        o = opts(api, nbins=nb, r_max_mm=3.0, seed=3)
+        g, code, flags = run_gpu(x, o)
+        assert code == 0
+        r = run_oracle(x, o)
+        for k in ("R", "T", "bins", "overflow"):
+            np.testing.assert_allclose(g[k][1:3], r[k][1:3], rtol=1e-5, atol=1e-6)
+        assert g["R"][0] == 0 and g["R"][3] == 0
+    # alpha = 0: no reflectance at all, whatever the boundary
+    x = inputs.single_wavelength(n_paths=5000).subset(np.arange(12, 14))
+    x.alpha[:] = 0.0
+    x.n_rel = 1.4
+    g, code, _ = run_gpu(x, opts(api))
+    assert np.all(g["R"] == 0) and np.all(g["R1"] == 0) and np.all(g["bins"] == 0)
+    # analog mode conserves path counts exactly
+    x = inputs.uneven_batch(n_inst=40, param_seed=5, log2_min=10, log2_max=12)
+    o = opts(api, mode=1, entry_fresnel=0, max_steps=256)
+    g, code, flags = run_gpu(x, o, raw=True)
+    nb = o.nbins
+    K = 3
+    raw = g["raw"].astype(np.uint64)
+    one = np.uint64(1) << np.uint64(32)
+    exits = (raw[:, :nb + 1].sum(1) + raw[:, nb + 2 + K] + raw[:, nb + 3 + K]) // one
+    assert np.all(exits + raw[:, nb + 4 + K] == x.n_paths)
+    # a step cap every path hits is flagged, not hung
+    o = opts(api, max_steps=1)
+    g, code, flags = run_gpu(x, o)
+    assert flags & 0x2 and code == 4
+    assert np.all(g["truncated"] + 0 <= x.n_paths)
+    # invalid parameter values are flagged by the device check
+    xb = x.subset(np.arange(x.n_inst))
+    xb.sigma_t[1, 3] = -1.0
+    g, code, flags = run_gpu(xb, opts(api))
+    assert flags & 0x1 and code == 6
