@@ -153,7 +153,12 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--texels", type=int, default=WORKLOAD["texels"],
+                    help="texels of the spectral field (smaller values: profiling cases)")
     args = ap.parse_args()
+    if args.texels != WORKLOAD["texels"]:
+        WORKLOAD["texels"] = args.texels
+        WORKLOAD["workload"] = f"spectral_field_{args.texels}texels_x81"
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -174,6 +179,7 @@ def main():
     m = api.Media.from_inputs(x, device=dev)
     o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=WORKLOAD["walk_seed"] + 7919 * rank)
     wsp = api.alloc_workspace(m, o)
+    wsp_bytes = wsp.numel()
     out = api.alloc_tallies(m, o)
     stream = torch.cuda.current_stream(dev)
     paths_per_step = int(x.n_paths.astype(np.int64).sum())
@@ -309,7 +315,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": dict(WORKLOAD, parallelism=f"replicas{ws}",
-                           l2="inputs (255 MB) and tally workspace (5.9 GB) exceed the 126 MB L2",
+                           l2=f"inputs ({x.alpha.nbytes * 4 / 1e6:.0f} MB) and tally workspace "
+                              f"({wsp_bytes / 1e9:.1f} GB) vs the 126 MB L2",
                            steps_per_path=steps_mean),
             "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps,
             "roofline": roofline, "cpu_baseline": cpu,

@@ -112,10 +112,10 @@ double oracle_fresnel(double cos_i, double n) {
   return 0.5 * (rs * rs + rp * rp);
 }
 
-/* Henyey-Greenstein cosine by inversion of its CDF; isotropic for |g|<1e-4. */
+/* Henyey-Greenstein cosine by inversion of its CDF (isotropic at g = 0). */
 double oracle_hg_mu(double g, double u) {
   double mu;
-  if (fabs(g) < 1e-4) {
+  if (g == 0.0) {
     mu = 2.0 * u - 1.0;
   } else {
     double t = (1.0 - g * g) / (1.0 - g + 2.0 * g * u);

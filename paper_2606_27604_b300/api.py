@@ -173,10 +173,12 @@ class Media:
         import numpy as np
         dev = torch.device(device)
         f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
-        uniform = np.all(x.n_paths == x.n_paths[0]) if per_instance_paths is None \
-            else not per_instance_paths
+        if per_instance_paths is None:
+            uniform = x.n_paths.size > 0 and bool(np.all(x.n_paths == x.n_paths[0]))
+        else:
+            uniform = not per_instance_paths
         n_paths = None if uniform else torch.from_numpy(
-            x.n_paths.astype(np.uint32).view(np.int32)).to(dev)
+            np.ascontiguousarray(x.n_paths, np.uint32).view(np.int32)).to(dev)
         return Media(f(x.alpha), f(x.sigma_t), f(x.g), f(x.w), n_paths,
                      int(x.n_paths[0]) if uniform else 0,
                      None if x.thickness_mm is None else f(x.thickness_mm), float(x.n_rel))

@@ -130,6 +130,7 @@ WalkConst make_const(const sss_params* p, const sss_walk_opts* o) {
   c.bin_scale = (float)((double)o->nbins / (double)o->r_max_mm);
   c.mode = o->mode;
   c.rr_th = o->mode == 0 ? o->rr_threshold : 0.0f;
+  c.inv_rr_th = c.rr_th > 0.0f ? (float)(1.0 / (double)c.rr_th) : 0.0f;
   c.max_steps = o->max_steps;
   c.key0 = (uint32_t)(o->seed & 0xffffffffull);
   c.key1 = (uint32_t)(o->seed >> 32);
@@ -181,7 +182,7 @@ sss_status persistent_shape(bool adj, const sss_params* p, const sss_walk_opts* 
   sh->burst = 1;
   sh->unit_paths = o->unit_paths ? (uint32_t)o->unit_paths : 1024u;
   // two slots of accumulators per warp; shrink the block for wide histograms
-  const size_t per_warp = (size_t)2 * acc_words * 8;
+  const size_t per_warp = (size_t)2 * acc_words * 8 + 2 * 32;  // + two 32-byte slot headers
   if (per_warp > kSmemLimit) return SSS_ERR_INVALID_ARG;
   const int max_warps = (int)(kSmemLimit / per_warp);
   if (sh->block / 32 > max_warps) sh->block = max_warps * 32;

@@ -40,9 +40,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// 23 random bits -> (k + 1/2) * 2^-23, exact in binary32, strictly in (0,1).
+// 23 random bits k -> (k + 1/2) * 2^-23, exact in binary32, strictly in (0,1).
+// The bits become the mantissa of 1 + k 2^-23 in [1, 2); subtracting
+// 1 - 2^-24 (exact: both operands lie in [1/2, 2]) leaves (k + 1/2) 2^-23.
 __device__ __forceinline__ float u23(uint32_t x) {
-  return __fmul_rn(__uint2float_rn(x >> 9) + 0.5f, 1.1920928955078125e-07f);
+  return __fsub_rn(__uint_as_float(0x3f800000u | (x >> 9)), 0.99999994039535522f);
 }
 
 // ------------------------------------------------------------ arguments --
@@ -62,6 +64,7 @@ struct WalkConst {
   float bin_scale;   // nbins / r_max
   int mode;          // 0 weight + roulette, 1 analog
   float rr_th;       // roulette threshold
+  float inv_rr_th;   // 1 / rr_th (exact for the power-of-two default)
   uint32_t max_steps;
   uint32_t key0, key1;
   uint32_t path_offset;
@@ -79,6 +82,7 @@ struct Path {
   float L;        // path length inside the medium (adjoint)
   float G;        // sum of d log p_HG / d g (adjoint)
   int bin;        // exit bin on a top exit (nbins = overflow)
+  float gscale, glim, wsum;  // adjoint: fixed-point scale, per-path limit, sum(w)
 };
 
 // Medium choice: first k whose running binary32 CDF of w/sum(w) exceeds u.
@@ -135,35 +139,25 @@ __device__ __forceinline__ float fresnel(float cos_i, float n) {
   const float cos_t = __fsqrt_rn(__fmaf_rn(-sin_t, sin_t, 1.0f));
   const float nci = __fmul_rn(n, cos_i);
   const float nct = __fmul_rn(n, cos_t);
-  const float rs = __fdiv_rn(__fsub_rn(nci, cos_t), __fadd_rn(nci, cos_t));
-  const float rp = __fdiv_rn(__fsub_rn(cos_i, nct), __fadd_rn(cos_i, nct));
+  const float rs = __fdividef(__fsub_rn(nci, cos_t), __fadd_rn(nci, cos_t));
+  const float rp = __fdividef(__fsub_rn(cos_i, nct), __fadd_rn(cos_i, nct));
   return __fmul_rn(0.5f, __fmaf_rn(rs, rs, __fmul_rn(rp, rp)));
 }
 
-// Henyey-Greenstein cosine by CDF inversion.  With xi = 2u - 1 the textbook
-// inverse  mu = (1 + g^2 - ((1-g^2)/(1+g xi))^2) / (2g)  equals
-//   mu = (xi + (g/2)(3 + xi^2 + 2 g xi + g^2 (xi^2 - 1))) / (1 + g xi)^2,
-// which has no cancellation for small g; the textbook form is used for
-// |g| >= 1/4, where it is the better conditioned of the two.
+// Henyey-Greenstein cosine by CDF inversion.  With xi = 2u - 1, the textbook
+// inverse  mu = (1 + g^2 - ((1-g^2)/(1+g xi))^2) / (2g)  is rewritten,
+// multiplying out and dividing by g, as the branch-free
+//   mu = ((1 + g^2)(2 xi + g xi^2) + g (3 - g^2)) / (2 (1 + g xi)^2),
+// exact for every g in (-1, 1) (g = 0 gives mu = xi) and free of the
+// 1/g cancellation of the textbook form at small g.  Lanes holding media
+// with different g run the same instructions.
 __device__ __forceinline__ float hg_mu(float g, float u) {
   const float xi = __fsub_rn(__fmul_rn(2.0f, u), 1.0f);  // exact
-  float mu;
-  if (fabsf(g) < 1e-4f) {
-    mu = xi;
-  } else if (fabsf(g) < 0.25f) {
-    const float gx = __fmul_rn(g, xi);
-    const float den = __fadd_rn(1.0f, gx);
-    const float xi2 = __fmul_rn(xi, xi);
-    float br = __fadd_rn(3.0f, xi2);
-    br = __fmaf_rn(2.0f, gx, br);
-    br = __fmaf_rn(__fmul_rn(g, g), __fsub_rn(xi2, 1.0f), br);
-    const float num = __fmaf_rn(__fmul_rn(0.5f, g), br, xi);
-    mu = __fdiv_rn(num, __fmul_rn(den, den));
-  } else {
-    const float g2 = __fmul_rn(g, g);
-    const float t = __fdiv_rn(__fsub_rn(1.0f, g2), __fmaf_rn(g, xi, 1.0f));
-    mu = __fdiv_rn(__fmaf_rn(-t, t, __fadd_rn(1.0f, g2)), __fmul_rn(2.0f, g));
-  }
+  const float g2 = __fmul_rn(g, g);
+  const float a = __fmaf_rn(g, __fmul_rn(xi, xi), __fmul_rn(2.0f, xi));  // 2 xi + g xi^2
+  const float num = __fmaf_rn(__fadd_rn(1.0f, g2), a, __fmul_rn(g, __fsub_rn(3.0f, g2)));
+  const float den = __fmaf_rn(g, xi, 1.0f);
+  const float mu = __fdividef(num, __fmul_rn(2.0f, __fmul_rn(den, den)));
   return fminf(1.0f, fmaxf(-1.0f, mu));
 }
 
@@ -219,7 +213,7 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
     p.Aacc = __fmaf_rn(p.W, __fsub_rn(1.0f, p.alpha), p.Aacc);
     p.W = __fmul_rn(p.W, p.alpha);
     if (p.W < c.rr_th) {
-      if (u3 < __fdiv_rn(p.W, c.rr_th)) p.W = c.rr_th;
+      if (u3 < __fmul_rn(p.W, c.inv_rr_th)) p.W = c.rr_th;
       else return EV_DEAD;
     }
   } else {
@@ -244,8 +238,9 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
     ny = __fmul_rn(st, sp);
     nz = p.uz >= 0.0f ? mu : -mu;
   } else {
-    const float tmp = __fsqrt_rn(__fmaf_rn(-p.uz, p.uz, 1.0f));
-    const float itmp = __frcp_rn(tmp);
+    const float s2 = __fmaf_rn(-p.uz, p.uz, 1.0f);
+    const float itmp = rsqrtf(s2);
+    const float tmp = __fmul_rn(s2, itmp);
     const float sti = __fmul_rn(st, itmp);
     const float uzcp = __fmul_rn(p.uz, cp);
     nx = __fmaf_rn(sti, __fmaf_rn(p.ux, uzcp, -__fmul_rn(p.uy, sp)), __fmul_rn(p.ux, mu));

@@ -192,101 +192,182 @@ __device__ __forceinline__ int grad_exponent(const WalkConst& c, const GradIn& g
   return E;
 }
 
+// Warp-uniform state of one work unit held by a warp (kept in shared memory).
+struct SlotMeta {
+  uint32_t inst, next, end, live;
+  float d, scale, lim, wsum;
+};
+
+enum : int { LANE_IDLE = 0, LANE_RUNNING = 1, LANE_DONE = 2 };
+
+// Adds one finished path to its slot's shared accumulators.
+template <bool ADJ>
+__device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& s,
+                                           const GradIn& gi, const Path& p, int ev,
+                                           unsigned long long* m) {
+  if (!ADJ) {
+    const int nb = c.nbins;
+    if (ev == EV_TOP) {
+      const unsigned long long q = __float2ull_rn(__fmul_rn(p.W, kFix));
+      atomicAdd(m + p.bin, q);
+      atomicAdd(m + nb + 1 + p.k, q);
+      if (p.n_coll == 1u) atomicAdd(m + nb + 1 + c.K, q);
+      if (s.want_sumsq)
+        atomicAdd(m + nb + 6 + c.K + p.bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
+    } else if (ev == EV_BOTTOM) {
+      atomicAdd(m + nb + 2 + c.K, __float2ull_rn(__fmul_rn(p.W, kFix)));
+    } else if (ev == EV_TRUNC) {
+      atomicAdd(m + nb + 4 + c.K, 1ull);
+    }
+    if (p.Aacc > 0.0f) atomicAdd(m + nb + 3 + c.K, __float2ull_rn(__fmul_rn(p.Aacc, kFix)));
+    atomicAdd(m + nb + 5 + c.K, (unsigned long long)p.step);
+  } else {
+    float v = 0.0f;
+    if (ev == EV_TOP) {
+      double vd = 0.0;
+      if (gi.grad_R) vd += gi.grad_R[p.inst];
+      if (gi.grad_bins && p.bin < c.nbins) vd += gi.grad_bins[(size_t)p.inst * c.nbins + p.bin];
+      if (gi.grad_R_k) vd += gi.grad_R_k[(size_t)p.inst * c.K + p.k];
+      v = (float)vd;
+    } else if (ev == EV_BOTTOM) {
+      if (gi.grad_T) v = (float)gi.grad_T[p.inst];
+    }
+    if (v != 0.0f) {
+      const float Wv = __fmul_rn(__fmul_rn(p.W, v), p.gscale);
+      const float nf = (float)p.n_coll;
+      float q[4];
+      q[0] = __fmul_rn(Wv, __fdiv_rn(nf, p.alpha));
+      q[1] = __fmul_rn(Wv, __fsub_rn(__fmul_rn(nf, p.inv_sigt), p.L));
+      q[2] = __fmul_rn(Wv, p.G);
+      q[3] = __fmul_rn(Wv, __fdiv_rn(p.wsum, __ldg(c.w + (size_t)p.k * c.n_inst + p.inst)));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float x = q[j];
+        if (!(fabsf(x) < p.glim)) {
+          atomicOr(s.status, SSS_DEV_FLAG_OVERFLOW);
+          x = (x != x) ? 0.0f : copysignf(p.glim, x);
+        }
+        atomicAdd(m + j * c.K + p.k, (unsigned long long)__float2ll_rn(x));
+      }
+    }
+  }
+  if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
+}
+
 template <bool ADJ>
 __global__ void __launch_bounds__(256)
 walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   extern __shared__ unsigned long long smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
   const int slot_words = s.slot_words;
   unsigned long long* slot_mem = smem + (size_t)wib * 2 * slot_words;
+  SlotMeta* meta =
+      reinterpret_cast<SlotMeta*>(smem + (size_t)nwarps * 2 * slot_words) + 2 * wib;
   for (int j = lane; j < 2 * slot_words; j += 32) slot_mem[j] = 0ull;
+  if (lane < 2) meta[lane].live = 0u;
   __syncwarp();
 
-  // Warp-uniform slot state.
-  uint32_t s_inst[2] = {0u, 0u}, s_next[2] = {0u, 0u}, s_end[2] = {0u, 0u};
-  float s_d[2] = {0.0f, 0.0f};
-  float s_scale[2] = {1.0f, 1.0f};   // adjoint fixed-point scale
-  float s_lim[2] = {0.0f, 0.0f};     // adjoint per-path magnitude limit
-  float s_wsum[2] = {1.0f, 1.0f};
-  bool s_live[2] = {false, false};
-  int cur = 0;
-  bool more = true;
+  int cur = 0;        // slot new paths are drawn from (warp-uniform)
+  bool more = true;   // the global queue may still hold units (warp-uniform)
 
-  // Lane state.
-  bool valid = false;
+  int st = LANE_IDLE;
   int myslot = 0;
+  int ev = EV_CONTINUE;
   Path p;
   p.step = 0;
 
+  // Takes the next unit from the global queue into slot o.
   auto fetch = [&](int o) -> bool {
     unsigned long long u = 0;
     if (lane == 0) u = atomicAdd(s.unit_counter, 1ull);
     u = __shfl_sync(kFull, u, 0);
     const UnitRange r = unit_lookup(s, c, u);
     if (!r.ok) return false;
-    s_inst[o] = r.inst;
-    s_next[o] = r.p0;
-    s_end[o] = r.p1;
-    s_d[o] = c.thickness ? __ldg(c.thickness + r.inst) : __int_as_float(0x7f800000);
-    s_live[o] = true;
+    float scale = 1.0f, lim = 0.0f, wsum = 1.0f;
     if (ADJ) {
       const int E = grad_exponent(c, gi, r.inst, lane);
-      s_scale[o] = ldexpf(1.0f, E);
+      scale = ldexpf(1.0f, E);
       const uint32_t N = c.n_paths ? c.n_paths[r.inst] : c.uniform_paths;
       const int lgN = N > 1 ? 32 - __clz(N - 1) : 0;
-      s_lim[o] = ldexpf(1.0f, 62 - lgN);
-      float ws = 0.0f;
-      for (int k = 0; k < c.K; ++k) ws = __fadd_rn(ws, __ldg(c.w + (size_t)k * c.n_inst + r.inst));
-      s_wsum[o] = ws;
+      lim = ldexpf(1.0f, 62 - lgN);
+      wsum = 0.0f;
+      for (int k = 0; k < c.K; ++k)
+        wsum = __fadd_rn(wsum, __ldg(c.w + (size_t)k * c.n_inst + r.inst));
     }
+    if (lane == 0) {
+      SlotMeta sm;
+      sm.inst = r.inst;
+      sm.next = r.p0;
+      sm.end = r.p1;
+      sm.live = 1u;
+      sm.d = c.thickness ? __ldg(c.thickness + r.inst) : __int_as_float(0x7f800000);
+      sm.scale = scale;
+      sm.lim = lim;
+      sm.wsum = wsum;
+      meta[o] = sm;
+    }
+    __syncwarp();
     return true;
   };
 
+  // Moves slot o's accumulators to global memory (one atomic per nonzero word).
   auto flush = [&](int o) {
     __syncwarp();
     unsigned long long* m = slot_mem + (size_t)o * slot_words;
-    unsigned long long* dst = ADJ ? t.raw : t.raw + (size_t)s_inst[o] * slot_words;
+    const uint32_t inst = meta[o].inst;
     for (int j = lane; j < slot_words; j += 32) {
       const unsigned long long v = m[j];
       if (v != 0ull) {
-        if (ADJ) {
-          // layout [4][K][n_inst]
-          atomicAdd(dst + (size_t)j * c.n_inst + s_inst[o], v);
-        } else {
-          atomicAdd(dst + j, v);
-        }
+        if (ADJ) atomicAdd(t.raw + (size_t)j * c.n_inst + inst, v);  // [4][K][n_inst]
+        else atomicAdd(t.raw + (size_t)inst * slot_words + j, v);
         m[j] = 0ull;
       }
     }
     __syncwarp();
-    s_live[o] = false;
+    if (lane == 0) meta[o].live = 0u;
+    __syncwarp();
   };
 
   if (!fetch(0)) more = false;
 
   while (true) {
-    // ---------------- refill idle lanes (path regrouping) ----------------
-    unsigned idle = __ballot_sync(kFull, !valid);
-    const int n_idle = __popc(idle);
-    if (n_idle >= s.regroup || n_idle == 32) {
+    const unsigned not_running = __ballot_sync(kFull, st != LANE_RUNNING);
+    const int n_nr = __popc(not_running);
+    if (n_nr >= s.regroup || n_nr == 32) {
+      // ---- 1. finished lanes tally together (one divergent block) ----
+      if (st == LANE_DONE) {
+        tally_path<ADJ>(c, s, gi, p, ev, slot_mem + (size_t)myslot * slot_words);
+        st = LANE_IDLE;
+      }
+      // ---- 2. refill idle lanes from the current unit (regrouping) ----
+      unsigned idle = __ballot_sync(kFull, st == LANE_IDLE);
       while (idle != 0u) {
-        if (s_next[cur] < s_end[cur]) {
-          const uint32_t avail = s_end[cur] - s_next[cur];
-          const uint32_t take = min((uint32_t)__popc(idle), avail);
+        const uint32_t nxt = meta[cur].next, end = meta[cur].end;
+        if (meta[cur].live && nxt < end) {
+          const uint32_t take = min((uint32_t)__popc(idle), end - nxt);
           const int rank = __popc(idle & ((1u << lane) - 1u));
-          if (!valid && (uint32_t)rank < take) {
-            path_init(c, s_inst[cur], c.path_offset + s_next[cur] + rank, s_d[cur], p);
-            valid = true;
+          __syncwarp();
+          if (st == LANE_IDLE && (uint32_t)rank < take) {
+            path_init(c, meta[cur].inst, c.path_offset + nxt + rank, meta[cur].d, p);
+            if (ADJ) {
+              p.gscale = meta[cur].scale;
+              p.glim = meta[cur].lim;
+              p.wsum = meta[cur].wsum;
+            }
+            st = LANE_RUNNING;
             myslot = cur;
           }
-          s_next[cur] += take;
-          idle = __ballot_sync(kFull, !valid);
+          __syncwarp();
+          if (lane == 0) meta[cur].next = nxt + take;
+          __syncwarp();
+          idle = __ballot_sync(kFull, st == LANE_IDLE);
         } else {
           if (!more) break;
           const int o = cur ^ 1;
-          if (s_live[o]) {
-            if (__ballot_sync(kFull, valid && myslot == o) != 0u) break;  // still running
+          if (meta[o].live) {
+            if (__ballot_sync(kFull, st == LANE_RUNNING && myslot == o) != 0u) break;
             flush(o);
           }
           if (!fetch(o)) {
@@ -297,75 +378,19 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
         }
       }
     }
-    if (__ballot_sync(kFull, valid) == 0u) {
-      if (!more && s_next[cur] >= s_end[cur]) break;
+    if (__ballot_sync(kFull, st == LANE_RUNNING) == 0u) {
+      if (!more) break;
       continue;
     }
-
-    // ---------------- advance every live path by `burst` draws -----------
-    for (int it = 0; it < s.burst; ++it) {
-      if (valid) {
-        const int ev = path_step<ADJ>(c, p);
-        if (ev != EV_CONTINUE) {
-          unsigned long long* m = slot_mem + (size_t)myslot * slot_words;
-          if (!ADJ) {
-            const int nb = c.nbins;
-            if (ev == EV_TOP) {
-              const unsigned long long q = __float2ull_rn(__fmul_rn(p.W, kFix));
-              atomicAdd(m + p.bin, q);
-              atomicAdd(m + nb + 1 + p.k, q);
-              if (p.n_coll == 1u) atomicAdd(m + nb + 1 + c.K, q);
-              if (s.want_sumsq)
-                atomicAdd(m + nb + 6 + c.K + p.bin,
-                          __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
-            } else if (ev == EV_BOTTOM) {
-              atomicAdd(m + nb + 2 + c.K, __float2ull_rn(__fmul_rn(p.W, kFix)));
-            } else if (ev == EV_TRUNC) {
-              atomicAdd(m + nb + 4 + c.K, 1ull);
-            }
-            if (p.Aacc > 0.0f) atomicAdd(m + nb + 3 + c.K, __float2ull_rn(__fmul_rn(p.Aacc, kFix)));
-            atomicAdd(m + nb + 5 + c.K, (unsigned long long)p.step);
-          } else {
-            float v = 0.0f;
-            if (ev == EV_TOP) {
-              double vd = 0.0;
-              if (gi.grad_R) vd += gi.grad_R[p.inst];
-              if (gi.grad_bins && p.bin < c.nbins) vd += gi.grad_bins[(size_t)p.inst * c.nbins + p.bin];
-              if (gi.grad_R_k) vd += gi.grad_R_k[(size_t)p.inst * c.K + p.k];
-              v = (float)vd;
-            } else if (ev == EV_BOTTOM) {
-              if (gi.grad_T) v = (float)gi.grad_T[p.inst];
-            }
-            if (v != 0.0f) {
-              const float sc = s_scale[myslot];
-              const float lim = s_lim[myslot];
-              const float Wv = __fmul_rn(__fmul_rn(p.W, v), sc);
-              const float nf = (float)p.n_coll;
-              float q[4];
-              q[0] = __fmul_rn(Wv, __fdiv_rn(nf, p.alpha));
-              q[1] = __fmul_rn(Wv, __fsub_rn(__fmul_rn(nf, p.inv_sigt), p.L));
-              q[2] = __fmul_rn(Wv, p.G);
-              q[3] = __fmul_rn(Wv, __fdiv_rn(s_wsum[myslot], c.w[(size_t)p.k * c.n_inst + p.inst]));
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                float x = q[j];
-                if (!(fabsf(x) < lim)) {
-                  atomicOr(s.status, SSS_DEV_FLAG_OVERFLOW);
-                  x = (x != x) ? 0.0f : copysignf(lim, x);
-                }
-                atomicAdd(m + j * c.K + p.k, (unsigned long long)__float2ll_rn(x));
-              }
-            }
-          }
-          if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
-          valid = false;
-        }
-      }
+    // ---- advance every running path by one draw ----
+    if (st == LANE_RUNNING) {
+      ev = path_step<ADJ>(c, p);
+      if (ev != EV_CONTINUE) st = LANE_DONE;
     }
   }
-  // flush whatever is still held
+  __syncwarp();
   for (int o = 0; o < 2; ++o)
-    if (s_live[o]) flush(o);
+    if (meta[o].live) flush(o);
 }
 
 // ------------------------------------------------------------------ plain --

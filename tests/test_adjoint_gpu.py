@@ -1,0 +1,199 @@
+"""Path-replay adjoint (sss_walk_bwd) on the GPU, through the C ABI.
+
+Checked against the oracle's score-function gradient on the same Philox
+streams, against common-random-number finite differences of the GPU forward
+walk, against closed forms, and through the torch.autograd.Function.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import hfunction as hf
+from paper_2606_27604_b300 import inputs
+from gpu_helpers import to_oracle_opts
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_27604_b300 import api as a
+    return a
+
+
+def _grads_gpu(api, x, o, **g):
+    import torch
+    m = api.Media.from_inputs(x)
+    tg = {k: torch.from_numpy(np.ascontiguousarray(v, np.float64)).cuda()
+          for k, v in g.items() if v is not None}
+    d = api.walk_bwd(m, o, **tg)
+    torch.cuda.synchronize()
+    code, flags = api.read_status(d["_workspace"])
+    return {k: v.cpu().numpy() for k, v in d.items() if not k.startswith("_")}, code, flags
+
+
+def _upstream(x, nbins, seed=0):
+    rng = np.random.default_rng(seed)
+    n = x.n_inst
+    return dict(grad_R=rng.normal(size=n), grad_bins=rng.normal(size=(n, nbins)),
+                grad_R_k=rng.normal(size=(n, x.K)))
+
+
+def test_adjoint_matches_oracle_score_gradient(api):
+    x = inputs.spectral_field(n_texels=3, param_seed=3, n_paths=8192)
+    o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1003)
+    up = _upstream(x, 64)
+    g, code, flags = _grads_gpu(api, x, o, **up)
+    assert code == 0 and flags == 0
+    r = oracle.walk_grad(x.alpha, x.sigma_t, x.g, x.w, x.n_paths, None, x.n_rel,
+                         to_oracle_opts(o), **up)
+    for k in ("d_alpha", "d_sigma_t", "d_g", "d_w"):
+        a, b, se = g[k], r[k], r["se_" + k]
+        # statistical bar and the tighter same-stream bound
+        assert np.all(np.abs(a - b) <= 4 * math.sqrt(2) * se + 1e-12), k
+        tight = 1e-4 * np.abs(b) + 0.25 * se + 1e-12
+        ratio = np.abs(a - b) / tight
+        print(k, "worst same-stream ratio", ratio.max())
+        assert ratio.max() <= 1.0, k
+
+
+def test_alpha_gradient_equals_crn_finite_difference(api):
+    # Roulette off: path geometry does not depend on alpha, so the forward
+    # estimate is a polynomial in alpha and the replay gives its derivative.
+    # Central differences at h and h/2, Richardson-combined to cancel the
+    # h^2 term (paths with hundreds of collisions have large curvature).
+    x = inputs.spectral_field(n_texels=2, param_seed=8, n_paths=4096)
+    x.alpha[:] = np.minimum(x.alpha, np.float32(0.99))
+    o = api.WalkOptions(nbins=32, r_max_mm=8.0, seed=4, rr_threshold=0.0, max_steps=4096)
+    g, code, _ = _grads_gpu(api, x, o, grad_R=np.ones(x.n_inst))
+
+    def fd(k, h):
+        xp = x.subset(np.arange(x.n_inst)); xm = x.subset(np.arange(x.n_inst))
+        xp.alpha[k] += np.float32(h); xm.alpha[k] -= np.float32(h)
+        step = xp.alpha[k].astype(np.float64) - xm.alpha[k].astype(np.float64)
+        Rp = api.walk(api.Media.from_inputs(xp), o)["R"].cpu().numpy()
+        Rm = api.walk(api.Media.from_inputs(xm), o)["R"].cpu().numpy()
+        return (Rp - Rm) / step
+
+    for k in range(3):
+        f1, f2 = fd(k, 4e-4), fd(k, 2e-4)
+        rich = (4.0 * f2 - f1) / 3.0
+        np.testing.assert_allclose(g["d_alpha"][k], rich, rtol=2e-3, atol=2e-6)
+
+
+def test_alpha_gradient_matches_h_function_derivative(api):
+    x = inputs.single_wavelength(n_paths=1 << 22).subset(np.array([2, 5]))  # alpha 0.5, 0.9
+    o = api.WalkOptions(nbins=32, r_max_mm=10.0, seed=21)
+    g, code, _ = _grads_gpu(api, x, o, grad_R=np.ones(2))
+    xs = x.subset(np.arange(2)); xs.n_paths = np.full(2, 1 << 16, np.uint32)
+    r = oracle.walk_grad(xs.alpha, xs.sigma_t, xs.g, xs.w, xs.n_paths, None, 1.0,
+                         to_oracle_opts(o), grad_R=np.ones(2))
+    se = np.sqrt((r["se_d_alpha"] ** 2).sum(0)) / math.sqrt(64)   # scaled to 2^22 paths
+    for i, a in enumerate((0.5, 0.9)):
+        ref = hf.reflectance_total_dalpha(float(np.float32(a)))
+        assert abs(g["d_alpha"][:, i].sum() - ref) <= 4 * se[i] + 1e-3 * ref
+
+
+def test_sigma_t_gradient_pins(api):
+    # semi-infinite: R does not depend on sigma_t (separability, Eq. 5)
+    x = inputs.single_wavelength(n_paths=1 << 20).subset(np.arange(10, 14))
+    x.n_rel = 1.4
+    o = api.WalkOptions(nbins=32, r_max_mm=10.0, seed=31)
+    g, _, _ = _grads_gpu(api, x, o, grad_R=np.ones(x.n_inst))
+    r = oracle.walk_grad(x.alpha, x.sigma_t, x.g, x.w, np.full(x.n_inst, 1 << 16, np.uint32),
+                         None, 1.4, to_oracle_opts(o), grad_R=np.ones(x.n_inst))
+    se = np.sqrt((r["se_d_sigma_t"] ** 2).sum(0)) / 4.0
+    assert np.all(np.abs(g["d_sigma_t"].sum(0)) <= 4 * se)
+    # ballistic slab: alpha = 0, n = 1, dT/dsigma_t = -d exp(-sigma_t d)
+    y = inputs.single_wavelength(n_paths=1 << 20).subset(np.arange(3))
+    y.alpha[:] = 0.0
+    y.thickness_mm = np.array([0.3, 0.8, 2.0], np.float32)
+    o2 = api.WalkOptions(nbins=8, r_max_mm=1.0, seed=5, mode=1, entry_fresnel=0)
+    g2, _, _ = _grads_gpu(api, y, o2, grad_T=np.ones(3))
+    d = y.thickness_mm.astype(np.float64)
+    st = y.sigma_t[0].astype(np.float64)
+    ref = -d * np.exp(-st * d)
+    p = np.exp(-st * d)
+    se = d * np.sqrt(p * (1 - p) / (1 << 20))
+    assert np.all(np.abs(g2["d_sigma_t"].sum(0) - ref) <= 4 * se + 1e-6)
+
+
+def test_weight_gradient_is_per_medium_reflectance(api):
+    import torch
+    x = inputs.spectral_field(n_texels=2, param_seed=12, n_paths=16384)
+    o = api.WalkOptions(nbins=32, r_max_mm=10.0, seed=8)
+    g, _, flags = _grads_gpu(api, x, o, grad_R=np.ones(x.n_inst))
+    f = api.walk(api.Media.from_inputs(x), o)
+    Rk = f["R_k"].cpu().numpy()                 # [n][K]
+    wsum = x.w.astype(np.float32).sum(0)
+    expect = (Rk.T * wsum / x.w)                 # same paths, same weights
+    np.testing.assert_allclose(g["d_w"], expect, rtol=1e-5, atol=1e-7)
+
+
+def test_adjoint_is_deterministic_across_launch_shapes(api):
+    x = inputs.uneven_batch(n_inst=200, param_seed=4, log2_min=8, log2_max=13)
+    up = _upstream(x, 48, seed=3)
+    base = api.WalkOptions(nbins=48, r_max_mm=6.0, seed=17)
+    ref, code, _ = _grads_gpu(api, x, base, **up)
+    assert code == 0
+    for kw in ({}, {"block_threads": 64}, {"unit_paths": 100, "regroup": 1}):
+        o = api.WalkOptions(nbins=48, r_max_mm=6.0, seed=17, **kw)
+        got, _, _ = _grads_gpu(api, x, o, **up)
+        for k in ref:
+            np.testing.assert_array_equal(ref[k], got[k], err_msg=f"{k} {kw}")
+
+
+def test_autograd_function_routes_to_replay(api):
+    import torch
+    x = inputs.spectral_field(n_texels=1, param_seed=6, n_paths=4096)
+    o = api.WalkOptions(nbins=16, r_max_mm=5.0, seed=2)
+    m = api.Media.from_inputs(x)
+    params = [t.clone().requires_grad_(True) for t in (m.alpha, m.sigma_t, m.g, m.w)]
+    R, bins, Rk = api.SSSWalk.apply(*params, m, o)
+    cB = torch.linspace(-1, 1, 16, device="cuda", dtype=torch.float64)
+    loss = (R * 2.0).sum() + (bins * cB).sum() + Rk[:, 1].sum()
+    grads = torch.autograd.grad(loss, params)
+    gB = cB.expand(m.n_inst, 16).contiguous()
+    gK = torch.zeros(m.n_inst, 3, device="cuda", dtype=torch.float64); gK[:, 1] = 1.0
+    d = api.walk_bwd(m, o, grad_R=torch.full((m.n_inst,), 2.0, device="cuda",
+                                               dtype=torch.float64), grad_bins=gB, grad_R_k=gK)
+    for gr, k in zip(grads, ("d_alpha", "d_sigma_t", "d_g", "d_w")):
+        torch.testing.assert_close(gr, d[k].float())
+
+
+def test_inverse_fit_recovers_albedo(api):
+    # Targets from held-out parameters; fit the three albedo spectra of a few
+    # texels by gradient descent on (R, radial bins) through the replay adjoint.
+    import torch
+    truth = inputs.spectral_field(n_texels=2, param_seed=33, n_paths=8192)
+    o = api.WalkOptions(nbins=32, r_max_mm=10.0, seed=1003)
+    mt = api.Media.from_inputs(truth)
+    tgt = api.walk(mt, o)
+    tR, tB = tgt["R"].clone(), tgt["bins"].clone()
+    alpha0 = torch.clamp(mt.alpha + 0.08 * torch.sign(torch.randn_like(mt.alpha)), 0.3, 0.999)
+    logit = torch.logit(alpha0).clone().requires_grad_(True)
+    opt = torch.optim.Adam([logit], lr=0.05)
+    err0 = None
+    for it in range(60):
+        a = torch.sigmoid(logit)
+        R, bins, _ = api.SSSWalk.apply(a, mt.sigma_t, mt.g, mt.w, mt, o)
+        loss = ((R - tR) ** 2).sum() + ((bins - tB) ** 2).sum()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        if err0 is None:
+            err0 = float(loss)
+    final = float(loss)
+    print("inverse fit loss", err0, "->", final)
+    assert final < 0.05 * err0
+    # albedo of the heaviest medium per band is recovered where it matters
+    a = torch.sigmoid(logit).detach()
+    heavy = mt.w.argmax(0)
+    idx = torch.arange(mt.n_inst, device="cuda")
+    err = (a[heavy, idx] - mt.alpha[heavy, idx]).abs()
+    assert float(err.median()) < 0.02
