@@ -165,6 +165,36 @@ def uneven_batch(n_inst: int = 4096, param_seed: int = 2, log2_min: float = 10.0
                       meta=dict(name="uneven_batch", param_seed=param_seed))
 
 
+# Layer widths of the chained decoder (Sec. 5.1): the encoder and reflectance
+# decoder widths are not given in the paper (it defers to a cited work), so
+# these two are stand-ins; Dec_T is 381 -> 768 -> 768 -> 768 -> 376 x 12.
+DECODER_WIDTHS = {
+    "enc": (3, 256, 256, 5),
+    "dec_r": (5, 512, 512, 376),
+    "dec_t": (381, 768, 768, 768, 376 * 12),
+}
+
+
+def decoder_weights(seed: int = 4) -> dict:
+    """Seeded random-init weights of the chained decoder (no trained weights
+    are available).  Uniform Xavier init, biases U(-0.1, 0.1).  Values are
+    rounded to bfloat16 (returned as float32 holding bf16 values) so that
+    every consumer sees the same numbers.  Weight matrices are [out][in]."""
+    import torch
+    rng = np.random.default_rng(seed)
+    out = {}
+    for net, dims in DECODER_WIDTHS.items():
+        for l in range(len(dims) - 1):
+            fan_in, fan_out = dims[l], dims[l + 1]
+            lim = np.sqrt(6.0 / (fan_in + fan_out))
+            W = rng.uniform(-lim, lim, size=(fan_out, fan_in))
+            b = rng.uniform(-0.1, 0.1, size=fan_out)
+            Wb = torch.from_numpy(W.astype(np.float32)).to(torch.bfloat16).float().numpy()
+            bb = torch.from_numpy(b.astype(np.float32)).to(torch.bfloat16).float().numpy()
+            out[f"{net}{l}"] = (Wb, bb)
+    return out
+
+
 def rgb_texture(side: int = 1024, seed: int = 4) -> np.ndarray:
     """float32 [side*side][3] RGB albedo from a 3-component Gaussian mixture
     per channel, clipped to [0.05, 0.85]."""
