@@ -51,7 +51,8 @@ typedef enum {
   SSS_ERR_STEP_LIMIT = 4,   /* device: some paths hit the step cap */
   SSS_ERR_OVERFLOW = 5,     /* device: a fixed-point accumulator saturated */
   SSS_ERR_DEVICE_PARAM = 6, /* device: a parameter value is out of range */
-  SSS_ERR_UNSUPPORTED = 7   /* no sm_103a device, or a feature not built */
+  SSS_ERR_UNSUPPORTED = 7,  /* no sm_103a device, or a feature not built */
+  SSS_ERR_TIMEOUT = 8       /* device: a bounded wait gave up (decoder pipeline) */
 } sss_status;
 
 /* Device status word bits (sss_read_status). */
@@ -59,6 +60,7 @@ typedef enum {
 #define SSS_FLAG_STEP_LIMIT 0x2u /* at least one path was truncated */
 #define SSS_FLAG_OVERFLOW 0x4u   /* a gradient accumulator saturated */
 #define SSS_FLAG_ZERO_WEIGHT 0x8u /* a medium with w_k = 0 got a zero gradient */
+#define SSS_FLAG_TIMEOUT 0x10u    /* a pipeline wait gave up (outputs undefined) */
 
 typedef void* sss_stream_t; /* cudaStream_t */
 
@@ -231,6 +233,48 @@ sss_status sss_read_status(const void* workspace, sss_stream_t stream, uint32_t*
  * (diagnostic): out[4*i .. 4*i+3] = Philox(ctr[4*i .. 4*i+3], key).
  * ctr, out: device uint32 arrays of 4*n words. */
 sss_status sss_philox(const uint32_t* ctr, uint64_t key, int64_t n, uint32_t* out,
+                      sss_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Chained decoder (paper Sec. 5.1, Eq. 10): RGB albedo -> Enc -> p (5) ->
+ * Dec_R -> R_d (376 bands, 250-1000 nm at 2 nm) -> Dec_T(p, R_d) ->
+ * theta(lambda) = {alpha_k, g_k, sigma_t,k, w_k}, K = 3, then resampled
+ * linearly to the 81 visible bands 380-780 nm at 5 nm.  BF16 operands on the
+ * tensor cores, FP32 accumulation, BF16 hidden activations.
+ * Layers (natural layout W [out][in], bf16 bits as uint16, device; b [out]
+ * float32, device), in this order:
+ *   0 enc0  3 -> 256 tanh      1 enc1 256 -> 256 tanh   2 enc2 256 -> 5 sigmoid
+ *   3 dec_r0 5 -> 512 tanh     4 dec_r1 512 -> 512 tanh 5 dec_r2 512 -> 376 sigmoid
+ *   6 dec_t0 381 -> 768 tanh (input order: p then R_d)
+ *   7 dec_t1 768 -> 768 tanh   8 dec_t2 768 -> 768 tanh
+ *   9 dec_t3 768 -> 376*12, output index  band*12 + k*4 + c  with channel c
+ *     0 alpha (sigmoid), 1 g (sigmoid), 2 sigma_t = 10^(3 sigmoid) mm^-1,
+ *     3 w (softmax over k).
+ * The Enc / Dec_R widths are stand-ins (the paper defers them to a cited
+ * work); Dec_T's are the paper's. */
+typedef struct {
+  const uint16_t* W[10];
+  const float* b[10];
+} sss_decoder_weights;
+
+/* Bytes of the packed (padded, reordered) weights sss_decode reads. */
+size_t sss_decoder_packed_size(void);
+
+/* Packs the natural-layout weights into `packed` (device, 256-byte aligned,
+ * sss_decoder_packed_size() bytes) with kernels on `stream`. */
+sss_status sss_decoder_pack(const sss_decoder_weights* w, void* packed, size_t packed_bytes,
+                            sss_stream_t stream);
+
+/* Workspace bytes sss_decode needs for T texels (activation buffers). */
+size_t sss_decode_workspace_size(int64_t T);
+
+/* Decodes T texels: rgb float32 [T][3] (device) -> float32 alpha, g,
+ * sigma_t, w, each [3][81 * T] (device, caller-owned), in the walk's
+ * sss_params layout with instance i = band * T + texel (band-major).
+ * workspace: 256-byte aligned, sss_decode_workspace_size(T) bytes; its first
+ * word is the status word (sss_read_status: SSS_FLAG_TIMEOUT). */
+sss_status sss_decode(const float* rgb, int64_t T, const void* packed, void* workspace,
+                      size_t workspace_bytes, float* alpha, float* g, float* sigma_t, float* w,
                       sss_stream_t stream);
 
 /* Profiling hook.  With both events non-NULL (cudaEvent_t handles created by

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libsss.so")
 SSS_OK = 0
 STATUS_NAMES = {0: "SSS_OK", 1: "SSS_ERR_INVALID_ARG", 2: "SSS_ERR_CUDA",
                 3: "SSS_ERR_WORKSPACE", 4: "SSS_ERR_STEP_LIMIT", 5: "SSS_ERR_OVERFLOW",
-                6: "SSS_ERR_DEVICE_PARAM", 7: "SSS_ERR_UNSUPPORTED"}
+                6: "SSS_ERR_DEVICE_PARAM", 7: "SSS_ERR_UNSUPPORTED", 8: "SSS_ERR_TIMEOUT"}
 FLAG_PARAM, FLAG_STEP_LIMIT, FLAG_OVERFLOW, FLAG_ZERO_WEIGHT = 0x1, 0x2, 0x4, 0x8
 
 
@@ -311,3 +311,68 @@ class SSSWalk(torch.autograd.Function):
         cast = lambda t: t.to(torch.float32)
         return cast(d["d_alpha"]), cast(d["d_sigma_t"]), cast(d["d_g"]), cast(d["d_w"]), \
             None, None
+
+
+# ------------------------------------------------------------------ decoder --
+class DecoderWeights(C.Structure):
+    _fields_ = [("W", C.c_void_p * 10), ("b", C.c_void_p * 10)]
+
+
+DECODER_LAYERS = ("enc0", "enc1", "enc2", "dec_r0", "dec_r1", "dec_r2",
+                  "dec_t0", "dec_t1", "dec_t2", "dec_t3")
+
+
+def _decoder_sigs():
+    lib.sss_decoder_packed_size.argtypes = []
+    lib.sss_decoder_packed_size.restype = C.c_size_t
+    lib.sss_decode_workspace_size.argtypes = [C.c_int64]
+    lib.sss_decode_workspace_size.restype = C.c_size_t
+    lib.sss_decoder_pack.argtypes = [C.POINTER(DecoderWeights), C.c_void_p, C.c_size_t,
+                                     C.c_void_p]
+    lib.sss_decoder_pack.restype = C.c_int
+    lib.sss_decode.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t,
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.sss_decode.restype = C.c_int
+
+
+_decoder_sigs()
+
+
+def decoder_pack(weights: dict, device="cuda", stream=None) -> torch.Tensor:
+    """Packs natural-layout weights {name: (W [out][in], b [out])} (numpy or
+    torch, values representable in bf16) into the library's decoder layout."""
+    import numpy as np
+    keep = []
+    dw = DecoderWeights()
+    for i, name in enumerate(DECODER_LAYERS):
+        W, b = weights[name]
+        Wt = torch.as_tensor(np.asarray(W, np.float32)).to(torch.bfloat16).contiguous().to(device)
+        bt = torch.as_tensor(np.asarray(b, np.float32)).contiguous().to(device)
+        keep += [Wt, bt]
+        dw.W[i] = Wt.data_ptr()
+        dw.b[i] = bt.data_ptr()
+    n = lib.sss_decoder_packed_size()
+    packed = torch.empty(n, dtype=torch.uint8, device=device)
+    _check(lib.sss_decoder_pack(C.byref(dw), _ptr(packed), n, _stream(stream)),
+           "sss_decoder_pack")
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return packed
+
+
+def decode(rgb: torch.Tensor, packed: torch.Tensor, workspace: Optional[torch.Tensor] = None,
+           out: Optional[dict] = None, stream=None) -> dict:
+    """sss_decode: rgb float32 [T][3] CUDA -> dict alpha, g, sigma_t, w, each
+    float32 [3][81*T] (band-major instances, the walk's layout)."""
+    assert rgb.is_cuda and rgb.dtype == torch.float32 and rgb.is_contiguous()
+    T = rgb.shape[0]
+    if workspace is None:
+        workspace = torch.empty(lib.sss_decode_workspace_size(T), dtype=torch.uint8,
+                                device=rgb.device)
+    if out is None:
+        out = {k: torch.empty(3, 81 * T, dtype=torch.float32, device=rgb.device)
+               for k in ("alpha", "g", "sigma_t", "w")}
+    _check(lib.sss_decode(_ptr(rgb), T, _ptr(packed), _ptr(workspace), workspace.numel(),
+                          _ptr(out["alpha"]), _ptr(out["g"]), _ptr(out["sigma_t"]),
+                          _ptr(out["w"]), _stream(stream)), "sss_decode")
+    out["_workspace"] = workspace
+    return out

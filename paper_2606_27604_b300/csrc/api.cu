@@ -405,6 +405,7 @@ sss_status sss_read_status(const void* workspace, sss_stream_t stream, uint32_t*
       cudaStreamSynchronize(st) != cudaSuccess)
     return SSS_ERR_CUDA;
   *flags = h;
+  if (h & SSS_FLAG_TIMEOUT) return SSS_ERR_TIMEOUT;
   if (h & SSS_FLAG_PARAM) return SSS_ERR_DEVICE_PARAM;
   if (h & SSS_FLAG_OVERFLOW) return SSS_ERR_OVERFLOW;
   if (h & SSS_FLAG_STEP_LIMIT) return SSS_ERR_STEP_LIMIT;
@@ -441,6 +442,7 @@ const char* sss_status_string(sss_status s) {
     case SSS_ERR_OVERFLOW: return "fixed-point accumulator saturated";
     case SSS_ERR_DEVICE_PARAM: return "parameter value out of range";
     case SSS_ERR_UNSUPPORTED: return "unsupported device or feature";
+    case SSS_ERR_TIMEOUT: return "a bounded device wait gave up";
   }
   return "unknown status";
 }

@@ -1,0 +1,447 @@
+// decode.cu -- chained decoder MLP on the 5th-generation tensor cores.
+//
+// RGB albedo -> Enc -> p (5) -> Dec_R -> R_d (376 bands) -> Dec_T(R_d, p)
+// -> theta(lambda) = {alpha_k, g_k, sigma_t,k, w_k}, K = 3 (paper Sec. 5.1,
+// Eq. 10), resampled to the 81 visible bands and written as the walk's
+// structure-of-arrays parameters.
+//
+// Every layer but the first is one GEMM  C = act(A B^T + bias)  with BF16
+// operands and FP32 accumulation:
+//   * operands are staged by TMA (cp.async.bulk.tensor, 128-byte swizzle)
+//     into a 4-stage shared-memory ring guarded by mbarriers;
+//   * one thread issues tcgen05.mma (M = 128, N = BN, K = 16 per issue)
+//     with the accumulator in tensor memory (TMEM);
+//   * four epilogue warps read their 32 TMEM lanes with tcgen05.ld, add the
+//     bias, apply the activation and store: BF16 activations for hidden
+//     layers, or, for Dec_T's last layer, the per-band sigmoid / softmax /
+//     sigma_t map and the 376 -> 81 band resampling straight into the
+//     float32 parameter arrays.
+// The first layer (3 inputs) is a plain CUDA-core kernel.  Every wait on an
+// mbarrier gives up after about a second of clock cycles, sets a status bit
+// and lets the block finish.
+#include <cuda.h>  // CUtensorMap and its enums (types only; no driver calls linked)
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "decode_kernels.cuh"
+
+namespace sss {
+namespace dec {
+
+constexpr int BM = 128;
+constexpr int BK = 64;        // 64 bf16 = 128 bytes = one swizzle row
+constexpr int STAGES = 4;
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+// ------------------------------------------------------------- PTX glue --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile whose rows are 128 bytes,
+// 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride offset between 8-row groups
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major.
+template <int N>
+__device__ __forceinline__ constexpr uint32_t idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t addr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sigmoid_fast(float x) {
+  return __fmaf_rn(0.5f, tanh_fast(0.5f * x), 0.5f);
+}
+
+__device__ __forceinline__ float activate(float x, int act) {
+  return act == ACT_TANH ? tanh_fast(x) : act == ACT_SIGMOID ? sigmoid_fast(x) : x;
+}
+
+template <int BN>
+struct TmemCols {
+  static constexpr int value = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+};
+
+// ------------------------------------------------------------- the GEMM --
+template <int BN, int EPI>
+__global__ void __launch_bounds__(192, 1)
+gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
+                 const __grid_constant__ CUtensorMap tmap_b, int a_x0, int num_kb,
+                 const float* __restrict__ bias, EpiParams ep, unsigned int* status) {
+  constexpr int A_BYTES = BM * BK * 2;
+  constexpr int B_BYTES = BN * BK * 2;
+  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr int TCOLS = TmemCols<BN>::value;
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
+  static_assert(B_BYTES % 1024 == 0, "tiles must stay 1024-byte aligned");
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n_tile = blockIdx.x;
+  const int m_tile = blockIdx.y;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap_a))
+                   : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap_b))
+                   : "memory");
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u)) {
+          atomicOr(status, DEC_FLAG_TIMEOUT);
+          break;
+        }
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        uint8_t* sa = smem + s * STAGE_BYTES;
+        tma_load_2d(sa, &tmap_a, a_x0 + kb * BK, m_tile * BM, &full[s]);
+        tma_load_2d(sa + A_BYTES, &tmap_b, kb * BK, n_tile * BN, &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16<BN>();
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(&full[s], ph)) {
+          atomicOr(status, DEC_FLAG_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t b0 = a0 + A_BYTES;
+        const uint64_t da = smem_desc_sw128(a0), db = smem_desc_sw128(b0);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)  // K = 16 per MMA: advance 32 bytes
+          umma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+        umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+      }
+      umma_commit(done);
+    }
+  } else {
+    // ---------------------------- epilogue: warps 2..5 -------------------
+    const int q = warp & 3;  // TMEM lane quarter this warp may read
+    const int row = m_tile * BM + q * 32 + lane;
+    const bool wait_ok = mbar_wait(done, 0u);
+    if (!wait_ok && lane == 0) atomicOr(status, DEC_FLAG_TIMEOUT);
+    tc_fence_after();
+    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+    if (EPI == EPI_HIDDEN) {
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(taddr + c0, v);
+        tmem_wait_ld();
+        const int col = n_tile * BN + c0;
+        if (!wait_ok || row >= ep.M || col >= ep.n_valid) continue;
+        __nv_bfloat16 h[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float b = (col + j < ep.n_valid) ? __ldg(bias + col + j) : 0.0f;
+          h[j] = __float2bfloat16_rn(activate(v[j] + b, ep.act));
+        }
+        __nv_bfloat16* dst = ep.out + (size_t)row * ep.ldc + ep.col0 + col;
+        if (col + 16 <= ep.n_valid && ((ep.col0 + col) & 7) == 0 && (ep.ldc & 7) == 0) {
+          const uint4* src = reinterpret_cast<const uint4*>(h);
+          reinterpret_cast<uint4*>(dst)[0] = src[0];
+          reinterpret_cast<uint4*>(dst)[1] = src[1];
+        } else {
+          for (int j = 0; j < 16 && col + j < ep.n_valid; ++j) dst[j] = h[j];
+        }
+      }
+    } else {
+      // Dec_T's last layer.  Columns come in groups of 36 = 3 source bands x
+      // (K = 3 media x 4 channels): group P holds the source band of the
+      // even target band 2P and the two source bands halfway around the odd
+      // target band 2P+1.  Channels: alpha, g, sigma_t (sigmoid), w (softmax
+      // over the media).
+      for (int gq = 0; gq < BN / 36; ++gq) {
+        float v[36];
+        tmem_ld16(taddr + gq * 36, v);
+        tmem_ld16(taddr + gq * 36 + 16, v + 16);
+        tmem_ld4(taddr + gq * 36 + 32, v + 32);
+        tmem_wait_ld();
+        const int P = n_tile * (BN / 36) + gq;
+        if (!wait_ok || row >= ep.M || P >= ep.n_pairs) continue;
+        const float* bp = bias + (size_t)(n_tile * BN + gq * 36);
+        float a[3][3], gg[3][3], st[3][3], ww[3][3];  // [slot][k]
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl) {
+          float m = -3.0e38f;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int c = sl * 12 + k * 4;
+            a[sl][k] = sigmoid_fast(v[c + 0] + __ldg(bp + c + 0));
+            gg[sl][k] = sigmoid_fast(v[c + 1] + __ldg(bp + c + 1));
+            st[sl][k] = exp2f(3.0f * 3.3219280948873623f * sigmoid_fast(v[c + 2] + __ldg(bp + c + 2)));
+            ww[sl][k] = v[c + 3] + __ldg(bp + c + 3);
+            m = fmaxf(m, ww[sl][k]);
+          }
+          float z = 0.0f;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            ww[sl][k] = __expf(ww[sl][k] - m);
+            z += ww[sl][k];
+          }
+          const float iz = __fdividef(1.0f, z);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) ww[sl][k] *= iz;
+        }
+        const size_t T = (size_t)ep.T;
+        const size_t nin = T * (size_t)ep.n_dst;
+        const int je = 2 * P;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const size_t o = (size_t)k * nin + (size_t)je * T + row;
+          ep.alpha[o] = a[0][k];
+          ep.g[o] = gg[0][k];
+          ep.sigma_t[o] = st[0][k];
+          ep.w[o] = ww[0][k];
+        }
+        if (je + 1 < ep.n_dst) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const size_t o = (size_t)k * nin + (size_t)(je + 1) * T + row;
+            ep.alpha[o] = 0.5f * (a[1][k] + a[2][k]);
+            ep.g[o] = 0.5f * (gg[1][k] + gg[2][k]);
+            ep.sigma_t[o] = 0.5f * (st[1][k] + st[2][k]);
+            ep.w[o] = 0.5f * (ww[1][k] + ww[2][k]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TCOLS)
+                 : "memory");
+  }
+}
+
+// --------------------------------------------- first layer (CUDA cores) --
+// h = tanh(W rgb + b), W [256][3] bf16, rgb float32 [T][3] -> bf16 [T][256].
+__global__ void __launch_bounds__(256)
+enc0_kernel(const float* __restrict__ rgb, long long T, const __nv_bfloat16* __restrict__ W,
+            const float* __restrict__ b, __nv_bfloat16* __restrict__ out) {
+  __shared__ float sw[256 * 3 + 256];
+  for (int i = threadIdx.x; i < 256 * 4; i += blockDim.x)
+    sw[i] = i < 768 ? __bfloat162float(W[i]) : b[i - 768];
+  __syncthreads();
+  // one warp per texel row, each lane 8 outputs (16-byte store)
+  const long long rowg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (rowg >= T) return;
+  const float r = rgb[rowg * 3 + 0], g = rgb[rowg * 3 + 1], bl = rgb[rowg * 3 + 2];
+  __nv_bfloat16 h[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int o = lane * 8 + j;
+    const float z = __fmaf_rn(sw[o * 3 + 0], r,
+                              __fmaf_rn(sw[o * 3 + 1], g, __fmaf_rn(sw[o * 3 + 2], bl, sw[768 + o])));
+    h[j] = __float2bfloat16_rn(tanh_fast(z));
+  }
+  reinterpret_cast<uint4*>(out + rowg * 256)[lane] = *reinterpret_cast<const uint4*>(h);
+}
+
+// --------------------------------------------------------------- packing --
+// dst[r][c] (bf16, rows x cols) = src[rmap(r)][cmap(c)] or 0, for the layer
+// layouts the GEMMs read (padding, Dec_T input order, last-layer grouping).
+__global__ void pack_weights_kernel(const __nv_bfloat16* __restrict__ src, int src_rows,
+                                    int src_cols, __nv_bfloat16* __restrict__ dst, int rows,
+                                    int cols, int map_kind, const float* __restrict__ bsrc,
+                                    float* __restrict__ bdst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)rows * cols) return;
+  const int r = (int)(i / cols), c = (int)(i % cols);
+  int sr = r, sc = c;
+  if (map_kind == PACK_DECT_IN) {          // GPU order [R_d(376), p(5), 0...] <- paper [p, R_d]
+    sc = c < 376 ? c + 5 : (c < 381 ? c - 376 : -1);
+  } else if (map_kind == PACK_DECT_OUT) {  // grouped rows of the last layer
+    sr = dect_out_source_row(r);
+  }
+  const bool ok = sr >= 0 && sr < src_rows && sc >= 0 && sc < src_cols;
+  dst[i] = ok ? src[(size_t)sr * src_cols + sc] : __float2bfloat16_rn(0.0f);
+  if (c == 0 && bdst) bdst[r] = (sr >= 0 && sr < src_rows) ? bsrc[sr] : 0.0f;
+}
+
+// ---------------------------------------------------------------- launch --
+template <int BN, int EPI>
+static cudaError_t launch_gemm_t(const CUtensorMap& ta, const CUtensorMap& tb, int a_x0,
+                                 int num_kb, int n_tiles, long long m_tiles, const float* bias,
+                                 const EpiParams& ep, unsigned int* status, cudaStream_t st) {
+  constexpr size_t smem = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 + 256;
+  auto fn = gemm_bf16_kernel<BN, EPI>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)n_tiles, (unsigned)m_tiles);
+  fn<<<grid, 192, smem, st>>>(ta, tb, a_x0, num_kb, bias, ep, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(int bn, int epi, const CUtensorMap& ta, const CUtensorMap& tb, int a_x0,
+                        int num_kb, int n_tiles, long long m_tiles, const float* bias,
+                        const EpiParams& ep, unsigned int* status, cudaStream_t st) {
+  if (epi == EPI_FINAL && bn == 144)
+    return launch_gemm_t<144, EPI_FINAL>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st);
+  if (epi == EPI_HIDDEN) {
+    switch (bn) {
+      case 16: return launch_gemm_t<16, EPI_HIDDEN>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st);
+      case 128: return launch_gemm_t<128, EPI_HIDDEN>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st);
+      case 256: return launch_gemm_t<256, EPI_HIDDEN>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_enc0(const float* rgb, long long T, const __nv_bfloat16* W, const float* b,
+                        __nv_bfloat16* out, cudaStream_t st) {
+  if (T <= 0) return cudaSuccess;
+  const long long threads = T * 32;
+  enc0_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(rgb, T, W, b, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const __nv_bfloat16* src, int src_rows, int src_cols, __nv_bfloat16* dst,
+                        int rows, int cols, int map_kind, const float* bsrc, float* bdst,
+                        cudaStream_t st) {
+  const long long n = (long long)rows * cols;
+  pack_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, src_rows, src_cols, dst, rows,
+                                                                   cols, map_kind, bsrc, bdst);
+  return cudaGetLastError();
+}
+
+}  // namespace dec
+}  // namespace sss
