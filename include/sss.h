@@ -52,7 +52,8 @@ typedef enum {
   SSS_ERR_OVERFLOW = 5,     /* device: a fixed-point accumulator saturated */
   SSS_ERR_DEVICE_PARAM = 6, /* device: a parameter value is out of range */
   SSS_ERR_UNSUPPORTED = 7,  /* no sm_103a device, or a feature not built */
-  SSS_ERR_TIMEOUT = 8       /* device: a bounded wait gave up (decoder pipeline) */
+  SSS_ERR_TIMEOUT = 8,      /* device: a bounded wait gave up (decoder pipeline) */
+  SSS_ERR_TOO_LARGE = 9     /* needs more scratch than sss_walk_noalloc's built-in array */
 } sss_status;
 
 /* Device status word bits (sss_read_status). */
@@ -283,6 +284,33 @@ sss_status sss_decode(const float* rgb, int64_t T, const void* packed, void* wor
  * kernel, on the call's stream, so the caller can time that kernel alone.
  * Pass NULL, NULL to stop.  Ignored for calls replayed from a cached graph. */
 void sss_profile_events(void* start, void* stop);
+
+/* Forward walk for callers that cannot allocate device memory.  The paper
+ * has no counterpart to this entry point; it exists for hosts that own every
+ * device allocation themselves (a renderer plug-in inside an application
+ * with its own memory pool) or that must not call cudaMalloc on the calling
+ * thread (it can synchronise the device, and is not allowed while a stream is
+ * being captured).  It computes exactly what sss_walk computes, but its
+ * scratch lives in a fixed array inside the library:
+ *  - the array holds SSS_NOALLOC_SCRATCH_BYTES (16 MiB) on every GPU that
+ *    loads the library, until the process exits; calls whose
+ *    sss_walk_workspace_size exceeds it return SSS_ERR_TOO_LARGE (at 64 bins,
+ *    K = 3 and standard errors that is about 15,000 instances);
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture on that device;
+ *  - every call shares the one array, which keeps the last call's contents:
+ *    each call clears what must start at zero, but calls that overlap on
+ *    the GPU (other streams, other threads) race and must be serialised;
+ *  - it allocates nothing: no cudaMalloc / cudaFree and no allocating
+ *    library routine; schedule must be 0 and use_graph 0 (otherwise
+ *    SSS_ERR_INVALID_ARG).
+ * `out` as for sss_walk.  status_flags: NULL, or a host word that receives
+ * the device status word (the call then waits for `stream`, as
+ * sss_read_status does, and returns the mapped status). */
+#define SSS_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+sss_status sss_walk_noalloc(const sss_params* p, const sss_walk_opts* o, sss_tallies* out,
+                            uint32_t* status_flags, sss_stream_t stream);
 
 /* Drops every cached CUDA graph (use_graph = 1). */
 void sss_release_plans(void);

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libsss.so")
 SSS_OK = 0
 STATUS_NAMES = {0: "SSS_OK", 1: "SSS_ERR_INVALID_ARG", 2: "SSS_ERR_CUDA",
                 3: "SSS_ERR_WORKSPACE", 4: "SSS_ERR_STEP_LIMIT", 5: "SSS_ERR_OVERFLOW",
-                6: "SSS_ERR_DEVICE_PARAM", 7: "SSS_ERR_UNSUPPORTED", 8: "SSS_ERR_TIMEOUT"}
+                6: "SSS_ERR_DEVICE_PARAM", 7: "SSS_ERR_UNSUPPORTED", 8: "SSS_ERR_TIMEOUT",
+                9: "SSS_ERR_TOO_LARGE"}
 FLAG_PARAM, FLAG_STEP_LIMIT, FLAG_OVERFLOW, FLAG_ZERO_WEIGHT = 0x1, 0x2, 0x4, 0x8
 
 
@@ -376,3 +377,25 @@ def decode(rgb: torch.Tensor, packed: torch.Tensor, workspace: Optional[torch.Te
                           _ptr(out["w"]), _stream(stream)), "sss_decode")
     out["_workspace"] = workspace
     return out
+
+
+# ------------------------------------------------------- no-allocation walk --
+NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
+lib.sss_walk_noalloc.argtypes = [C.POINTER(Params), C.POINTER(Opts), C.POINTER(Tallies),
+                                 C.POINTER(C.c_uint32), C.c_void_p]
+lib.sss_walk_noalloc.restype = C.c_int
+
+
+def walk_noalloc(m: Media, o: WalkOptions, out: dict, stream=None):
+    """sss_walk_noalloc: the forward walk with the library's built-in scratch
+    (for callers that cannot allocate device memory).  `out` must already
+    hold the output tensors (alloc_tallies); returns (status, flags) after
+    waiting for the stream."""
+    t = Tallies(**{k: _ptr(out.get(k)) for k in
+                   ("R", "T", "A", "bins", "overflow", "R_k", "R1", "stderr_R",
+                    "stderr_bins", "truncated", "steps", "raw")})
+    p, oc = m.c(), o.c()
+    flags = C.c_uint32(0)
+    code = lib.sss_walk_noalloc(C.byref(p), C.byref(oc), C.byref(t), C.byref(flags),
+                                _stream(stream))
+    return code, flags.value

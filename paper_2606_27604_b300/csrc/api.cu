@@ -443,6 +443,8 @@ const char* sss_status_string(sss_status s) {
     case SSS_ERR_DEVICE_PARAM: return "parameter value out of range";
     case SSS_ERR_UNSUPPORTED: return "unsupported device or feature";
     case SSS_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case SSS_ERR_TOO_LARGE:
+      return "problem needs more scratch than the no-allocation entry point's built-in array";
   }
   return "unknown status";
 }
