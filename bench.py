@@ -37,6 +37,21 @@ ALG_ALU_OPS_PER_STEP = 120
 ALG_MUFU_OPS_PER_STEP = 6
 SM_LANES_PER_CLK = 128
 MUFU_LANES_PER_CLK = 16
+# Multiply-adds per texel of the chained decoder (unpadded): Enc 3-256-256-5,
+# Dec_R 5-512-512-376, Dec_T 381-768-768-768 and the 121 source bands x 12
+# outputs that the 81 visible bands need.
+DECODER_MACS_PER_TEXEL = (3 * 256 + 256 * 256 + 256 * 5) + (5 * 512 + 512 * 512 + 512 * 376) \
+    + (381 * 768 + 2 * 768 * 768 + 768 * 121 * 12)
+
+
+def _measured_peak(key, fallback):
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)[key])
+        return v, "of measured"
+    except (OSError, ValueError, KeyError):
+        return fallback, "of fallback"
 
 
 def _dist():
@@ -153,6 +168,11 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-baselines", action="store_true",
+                    help="skip the uneven-batch and plain one-launch-per-instance timings")
+    ap.add_argument("--no-decoder", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the walk kernel's launch shape with the autotuner first")
     ap.add_argument("--texels", type=int, default=WORKLOAD["texels"],
                     help="texels of the spectral field (smaller values: profiling cases)")
     args = ap.parse_args()
@@ -178,6 +198,9 @@ def main():
     x = spectral_inputs(rank)
     m = api.Media.from_inputs(x, device=dev)
     o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=WORKLOAD["walk_seed"] + 7919 * rank)
+    if args.autotune:
+        from paper_2606_27604_b300 import autotune
+        o = autotune.tune(m, o)
     wsp = api.alloc_workspace(m, o)
     wsp_bytes = wsp.numel()
     out = api.alloc_tallies(m, o)
@@ -291,6 +314,87 @@ def main():
                  "workload": "spectral_field_64x64x81 at 65536 paths, grads w.r.t. "
                              "(alpha, sigma_t, g, w) x 3 from upstream on R and 64 bins"}
 
+    # ---- batched uneven instances vs one launch per instance ---------------
+    baselines = None
+    if not args.no_baselines:
+        from paper_2606_27604_b300 import inputs
+
+        def timed(fn):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fn()
+            torch.cuda.synchronize()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / 1e3
+
+        xu = inputs.uneven_batch(n_inst=4096, param_seed=2)
+        mu_ = api.Media.from_inputs(xu, device=dev)
+        ou = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1002, use_graph=1)
+        wu = api.alloc_workspace(mu_, ou)
+        tu = api.alloc_tallies(mu_, ou)
+        t_graph = timed(lambda: api.walk(mu_, ou, workspace=wu, out=tu))
+        op = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1002, schedule=1)
+        t_plain = timed(lambda: api.walk(mu_, op, workspace=wu, out=tu))
+        pu = float(xu.n_paths.astype(np.float64).sum())
+        # plain baseline on a slice of the spectral workload (5.3 M launches
+        # for the whole field would be impractical): 2048 instances
+        xs = x.subset(np.arange(2048))
+        ms_ = api.Media.from_inputs(xs, device=dev)
+        wsb = api.alloc_workspace(ms_, o)
+        tsb = api.alloc_tallies(ms_, o)
+        from dataclasses import replace as _rep
+        t_sub_plain = timed(lambda: api.walk(ms_, _rep(o, schedule=1), workspace=wsb, out=tsb))
+        t_sub_pers = timed(lambda: api.walk(ms_, o, workspace=wsb, out=tsb))
+        ps = 2048.0 * WORKLOAD["paths_per_instance"]
+        baselines = {
+            "uneven_batch": {"workload": "4096 instances, budgets floor(2^U[10,20]) "
+                                         f"({pu:.3g} paths), finite and semi-infinite slabs",
+                             "persistent_graph_paths_per_s": pu / t_graph,
+                             "one_launch_per_instance_paths_per_s": pu / t_plain,
+                             "speedup": t_plain / t_graph},
+            "plain_on_spectral_slice": {"sample": "first 2048 instances of the spectral "
+                                                  "workload at 4096 paths",
+                                        "plain_paths_per_s": ps / t_sub_plain,
+                                        "persistent_paths_per_s_same_slice": ps / t_sub_pers},
+        }
+        api.release_plans()
+        del wu, tu, wsb, tsb
+
+    # ---- decoder (RGB -> per-band mixture parameters, tensor cores) --------
+    decoder = None
+    if not args.no_decoder:
+        from paper_2606_27604_b300 import inputs
+        side = 1024
+        rgb = torch.from_numpy(inputs.rgb_texture(side=side, seed=4)).to(dev)
+        packed = api.decoder_pack(inputs.decoder_weights(seed=4), device=dev)
+        dws = torch.empty(api.lib.sss_decode_workspace_size(side * side), dtype=torch.uint8,
+                          device=dev)
+        dout = {k: torch.empty(3, 81 * side * side, dtype=torch.float32, device=dev)
+                for k in ("alpha", "g", "sigma_t", "w")}
+        for _ in range(3):
+            api.decode(rgb, packed, workspace=dws, out=dout)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            api.decode(rgb, packed, workspace=dws, out=dout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dms = e0.elapsed_time(e1) / reps
+        flops = 2.0 * DECODER_MACS_PER_TEXEL * side * side
+        dcode, dflags = api.read_status(dws)
+        peak_bf16 = _measured_peak("bf16_tflops", 1792.8)
+        decoder = {"workload": f"{side}x{side} RGB texels -> 3 media x 81 bands",
+                   "ms": dms, "texels_per_s": side * side / (dms / 1e3),
+                   "achieved_tflops": flops / (dms / 1e3) / 1e12,
+                   "peak_tflops": peak_bf16[0], "peak_basis": peak_bf16[1],
+                   "frac": flops / (dms / 1e3) / 1e12 / peak_bf16[0],
+                   "flops_per_texel": 2 * DECODER_MACS_PER_TEXEL, "status": dcode}
+        del dws, dout
+
     # ---- roofline of the walk kernel --------------------------------------
     kmean = float(np.mean(kern))
     f_mhz = clk["sm_mhz"] if clk else 2032.0
@@ -320,7 +424,9 @@ def main():
                            steps_per_path=steps_mean),
             "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps,
             "roofline": roofline, "cpu_baseline": cpu,
-            "adjoint_forward_ratio": ratio, "status_flags": flags}
+            "adjoint_forward_ratio": ratio, "baselines": baselines, "decoder": decoder,
+            "launch_shape": {k: getattr(o, k) for k in ("block_threads", "unit_paths", "regroup")},
+            "status_flags": flags}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

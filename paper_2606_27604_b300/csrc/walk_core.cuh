@@ -76,12 +76,11 @@ struct Path {
   float x, y, z, ux, uy, uz;
   float W;        // current weight
   float Aacc;     // weight deposited by collisions
-  float alpha, sigt, inv_sigt, g, d;
+  float alpha, sigt, fl, g, d;  // fl = ln(2) / sigma_t (flight scale for log2)
   uint32_t step, path, inst, n_coll;
   int k;
   float L;        // path length inside the medium (adjoint)
   float G;        // sum of d log p_HG / d g (adjoint)
-  int bin;        // exit bin on a top exit (nbins = overflow)
   float gscale, glim, wsum;  // adjoint: fixed-point scale, per-path limit, sum(w)
 };
 
@@ -114,7 +113,7 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.k = k;
   p.alpha = __ldg(c.alpha + off);
   p.sigt = __ldg(c.sigma_t + off);
-  p.inv_sigt = __fdiv_rn(1.0f, p.sigt);
+  p.fl = __fmul_rn(0.693147180559945309f, __fdiv_rn(1.0f, p.sigt));
   p.g = __ldg(c.g + off);
   p.d = d;
   p.x = 0.0f; p.y = 0.0f; p.z = 0.0f;
@@ -127,21 +126,36 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.n_coll = 0u;
   p.L = 0.0f;
   p.G = 0.0f;
-  p.bin = 0;
 }
 
-// Unpolarised Fresnel reflectance, medium (index n) -> outside (index 1).
+// Hardware approximations (one MUFU operation each, a few ulp).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Unpolarised Fresnel reflectance, medium (index n) -> outside (index 1),
+// without branches: total internal reflection (n sin_i >= 1) and n = 1 are
+// selected at the end; the two quotients share one reciprocal.
 __device__ __forceinline__ float fresnel(float cos_i, float n) {
-  if (n == 1.0f) return 0.0f;
   const float sin2_i = fmaxf(0.0f, __fmaf_rn(-cos_i, cos_i, 1.0f));
-  const float sin_t = __fmul_rn(n, __fsqrt_rn(sin2_i));
-  if (sin_t >= 1.0f) return 1.0f;
-  const float cos_t = __fsqrt_rn(__fmaf_rn(-sin_t, sin_t, 1.0f));
+  const float sin_t = __fmul_rn(n, sqrt_approx(sin2_i));
+  const float cos_t = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-sin_t, sin_t, 1.0f)));
   const float nci = __fmul_rn(n, cos_i);
   const float nct = __fmul_rn(n, cos_t);
-  const float rs = __fdividef(__fsub_rn(nci, cos_t), __fadd_rn(nci, cos_t));
-  const float rp = __fdividef(__fsub_rn(cos_i, nct), __fadd_rn(cos_i, nct));
-  return __fmul_rn(0.5f, __fmaf_rn(rs, rs, __fmul_rn(rp, rp)));
+  const float sd = __fadd_rn(nci, cos_t), pd = __fadd_rn(cos_i, nct);
+  const float inv = rcp_approx(__fmul_rn(sd, pd));
+  const float rs = __fmul_rn(__fmul_rn(__fsub_rn(nci, cos_t), pd), inv);
+  const float rp = __fmul_rn(__fmul_rn(__fsub_rn(cos_i, nct), sd), inv);
+  float F = __fmul_rn(0.5f, __fmaf_rn(rs, rs, __fmul_rn(rp, rp)));
+  F = sin_t >= 1.0f ? 1.0f : F;
+  return n == 1.0f ? 0.0f : F;
 }
 
 // Henyey-Greenstein cosine by CDF inversion.  With xi = 2u - 1, the textbook
@@ -169,6 +183,10 @@ __device__ __forceinline__ float hg_dlogp_dg(float g, float mu) {
 }
 
 // One random-number draw of the walk.  Returns the event it ended in.
+// Mostly branch-free: every lane evaluates both the face (Fresnel) and the
+// collision (weighting, Henyey-Greenstein, rotation) arithmetic and selects
+// the outcome of the event it actually met, so lanes of a warp that meet
+// different events issue the same instructions.
 template <bool ADJ>
 __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
   if (p.step >= c.max_steps) return EV_TRUNC;
@@ -176,82 +194,79 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
   p.step++;
   const float u0 = u23(r.x), u1 = u23(r.y), u2 = u23(r.z), u3 = u23(r.w);
 
-  // Exponential free flight (transmittance of the medium).
-  const float s = __fmul_rn(-logf(u0), p.inv_sigt);
+  // Exponential free flight -ln(u0) / sigma_t, from the hardware log2
+  // (absolute error <= 2^-22 mean free paths near u0 = 1, 2 ulp elsewhere).
+  const float s = fmaxf(0.0f, __fmul_rn(-__log2f(u0), p.fl));
   // Distance to the face the path is heading to.
-  float db = __int_as_float(0x7f800000);  // +inf
-  const float iuz = __frcp_rn(p.uz);
-  if (p.uz < 0.0f) db = __fmul_rn(-p.z, iuz);
-  else if (p.uz > 0.0f) db = __fmul_rn(__fsub_rn(p.d, p.z), iuz);
+  const float iuz = rcp_approx(p.uz);
+  const float inf = __int_as_float(0x7f800000);
+  const float db = p.uz < 0.0f ? __fmul_rn(-p.z, iuz)
+                               : (p.uz > 0.0f ? __fmul_rn(__fsub_rn(p.d, p.z), iuz) : inf);
+  const bool hit = db <= s;
+  const bool top = p.uz < 0.0f;
+  const float dist = hit ? db : s;
+  p.x = __fmaf_rn(dist, p.ux, p.x);
+  p.y = __fmaf_rn(dist, p.uy, p.y);
+  p.z = hit ? (top ? 0.0f : p.d) : __fmaf_rn(dist, p.uz, p.z);
+  if (ADJ) p.L = __fadd_rn(p.L, dist);
 
-  if (db <= s) {
-    // Reaches the face: move onto it, then reflect or leave (Fresnel).
-    p.x = __fmaf_rn(db, p.ux, p.x);
-    p.y = __fmaf_rn(db, p.uy, p.y);
-    const bool top = p.uz < 0.0f;
-    p.z = top ? 0.0f : p.d;
-    if (ADJ) p.L = __fadd_rn(p.L, db);
-    const float F = fresnel(fabsf(p.uz), c.n_rel);
-    if (u1 < F) {
-      p.uz = -p.uz;
-      return EV_CONTINUE;
-    }
-    if (!top) return EV_BOTTOM;
-    const float rr = __fsqrt_rn(__fmaf_rn(p.x, p.x, __fmul_rn(p.y, p.y)));
-    const float fb = fminf(floorf(__fmul_rn(rr, c.bin_scale)), (float)c.nbins);
-    p.bin = (int)fb;
-    return EV_TOP;
-  }
+  // Face: smooth-dielectric Fresnel, reflect with probability F.
+  const float F = fresnel(fabsf(p.uz), c.n_rel);
+  const bool reflect = hit && (u1 < F);
 
-  // Collision inside the medium.
-  p.x = __fmaf_rn(s, p.ux, p.x);
-  p.y = __fmaf_rn(s, p.uy, p.y);
-  p.z = __fmaf_rn(s, p.uz, p.z);
-  if (ADJ) p.L = __fadd_rn(p.L, s);
-  p.n_coll++;
+  // Collision: albedo weighting with roulette, or analog absorption.
+  bool dead;
   if (c.mode == 0) {
-    p.Aacc = __fmaf_rn(p.W, __fsub_rn(1.0f, p.alpha), p.Aacc);
-    p.W = __fmul_rn(p.W, p.alpha);
-    if (p.W < c.rr_th) {
-      if (u3 < __fmul_rn(p.W, c.inv_rr_th)) p.W = c.rr_th;
-      else return EV_DEAD;
-    }
+    const float Wn = __fmul_rn(p.W, p.alpha);
+    const float An = __fmaf_rn(p.W, __fsub_rn(1.0f, p.alpha), p.Aacc);
+    const bool low = Wn < c.rr_th;
+    dead = !hit && low && !(u3 < __fmul_rn(Wn, c.inv_rr_th));
+    p.W = hit ? p.W : (low ? c.rr_th : Wn);
+    p.Aacc = hit ? p.Aacc : An;
   } else {
-    if (u3 >= p.alpha) {
-      p.Aacc = __fadd_rn(p.Aacc, p.W);
-      return EV_DEAD;
-    }
+    dead = !hit && (u3 >= p.alpha);
+    p.Aacc = dead ? __fadd_rn(p.Aacc, p.W) : p.Aacc;
   }
+  p.n_coll += hit ? 0u : 1u;
 
   // Henyey-Greenstein scattering with this medium's g.
   const float mu = hg_mu(p.g, u1);
-  if (ADJ) p.G = __fadd_rn(p.G, hg_dlogp_dg(p.g, mu));
+  if (ADJ) p.G = (hit || dead) ? p.G : __fadd_rn(p.G, hg_dlogp_dg(p.g, mu));
   // Azimuth phi = 2 pi u2; evaluated as phi - pi in (-pi, pi), then negated.
   float sp, cp;
   __sincosf(__fmul_rn(6.2831853071795865f, __fsub_rn(u2, 0.5f)), &sp, &cp);
   sp = -sp;
   cp = -cp;
-  const float st = __fsqrt_rn(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
-  float nx, ny, nz;
-  if (fabsf(p.uz) > 0.999999f) {
-    nx = __fmul_rn(st, cp);
-    ny = __fmul_rn(st, sp);
-    nz = p.uz >= 0.0f ? mu : -mu;
-  } else {
-    const float s2 = __fmaf_rn(-p.uz, p.uz, 1.0f);
-    const float itmp = rsqrtf(s2);
-    const float tmp = __fmul_rn(s2, itmp);
-    const float sti = __fmul_rn(st, itmp);
-    const float uzcp = __fmul_rn(p.uz, cp);
-    nx = __fmaf_rn(sti, __fmaf_rn(p.ux, uzcp, -__fmul_rn(p.uy, sp)), __fmul_rn(p.ux, mu));
-    ny = __fmaf_rn(sti, __fmaf_rn(p.uy, uzcp, __fmul_rn(p.ux, sp)), __fmul_rn(p.uy, mu));
-    nz = __fmaf_rn(-__fmul_rn(st, cp), tmp, __fmul_rn(p.uz, mu));
-  }
+  const float st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
+  const float s2 = __fmaf_rn(-p.uz, p.uz, 1.0f);
+  const float itmp = rsqrtf(s2);
+  const float tmp = __fmul_rn(s2, itmp);
+  const float sti = __fmul_rn(st, itmp);
+  const float uzcp = __fmul_rn(p.uz, cp);
+  const bool polar = fabsf(p.uz) > 0.999999f;
+  const float nx = polar ? __fmul_rn(st, cp)
+                         : __fmaf_rn(sti, __fmaf_rn(p.ux, uzcp, -__fmul_rn(p.uy, sp)),
+                                     __fmul_rn(p.ux, mu));
+  const float ny = polar ? __fmul_rn(st, sp)
+                         : __fmaf_rn(sti, __fmaf_rn(p.uy, uzcp, __fmul_rn(p.ux, sp)),
+                                     __fmul_rn(p.uy, mu));
+  const float nz = polar ? (p.uz >= 0.0f ? mu : -mu)
+                         : __fmaf_rn(-__fmul_rn(st, cp), tmp, __fmul_rn(p.uz, mu));
   const float inr = rsqrtf(__fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz))));
-  p.ux = __fmul_rn(nx, inr);
-  p.uy = __fmul_rn(ny, inr);
-  p.uz = __fmul_rn(nz, inr);
+  const float uz_new = hit ? (reflect ? -p.uz : p.uz) : __fmul_rn(nz, inr);
+  p.ux = hit ? p.ux : __fmul_rn(nx, inr);
+  p.uy = hit ? p.uy : __fmul_rn(ny, inr);
+  p.uz = uz_new;
+
+  if (dead) return EV_DEAD;
+  if (hit && !reflect) return top ? EV_TOP : EV_BOTTOM;
   return EV_CONTINUE;
+}
+
+// Radial bin of a top exit (nbins = overflow).
+__device__ __forceinline__ int exit_bin(const WalkConst& c, const Path& p) {
+  const float rr = sqrt_approx(__fmaf_rn(p.x, p.x, __fmul_rn(p.y, p.y)));
+  return (int)fminf(floorf(__fmul_rn(rr, c.bin_scale)), (float)c.nbins);
 }
 
 }  // namespace sss

@@ -208,12 +208,13 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
   if (!ADJ) {
     const int nb = c.nbins;
     if (ev == EV_TOP) {
+      const int bin = exit_bin(c, p);
       const unsigned long long q = __float2ull_rn(__fmul_rn(p.W, kFix));
-      atomicAdd(m + p.bin, q);
+      atomicAdd(m + bin, q);
       atomicAdd(m + nb + 1 + p.k, q);
       if (p.n_coll == 1u) atomicAdd(m + nb + 1 + c.K, q);
       if (s.want_sumsq)
-        atomicAdd(m + nb + 6 + c.K + p.bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
+        atomicAdd(m + nb + 6 + c.K + bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
     } else if (ev == EV_BOTTOM) {
       atomicAdd(m + nb + 2 + c.K, __float2ull_rn(__fmul_rn(p.W, kFix)));
     } else if (ev == EV_TRUNC) {
@@ -224,9 +225,10 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
   } else {
     float v = 0.0f;
     if (ev == EV_TOP) {
+      const int bin = exit_bin(c, p);
       double vd = 0.0;
       if (gi.grad_R) vd += gi.grad_R[p.inst];
-      if (gi.grad_bins && p.bin < c.nbins) vd += gi.grad_bins[(size_t)p.inst * c.nbins + p.bin];
+      if (gi.grad_bins && bin < c.nbins) vd += gi.grad_bins[(size_t)p.inst * c.nbins + bin];
       if (gi.grad_R_k) vd += gi.grad_R_k[(size_t)p.inst * c.K + p.k];
       v = (float)vd;
     } else if (ev == EV_BOTTOM) {
@@ -237,7 +239,7 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
       const float nf = (float)p.n_coll;
       float q[4];
       q[0] = __fmul_rn(Wv, __fdiv_rn(nf, p.alpha));
-      q[1] = __fmul_rn(Wv, __fsub_rn(__fmul_rn(nf, p.inv_sigt), p.L));
+      q[1] = __fmul_rn(Wv, __fsub_rn(__fdiv_rn(nf, p.sigt), p.L));
       q[2] = __fmul_rn(Wv, p.G);
       q[3] = __fmul_rn(Wv, __fdiv_rn(p.wsum, __ldg(c.w + (size_t)p.k * c.n_inst + p.inst)));
 #pragma unroll
@@ -412,12 +414,13 @@ walk_plain_kernel(WalkConst c, WalkSched s, TallyOut t, uint32_t inst, uint32_t 
     } while (ev == EV_CONTINUE);
     const int nb = c.nbins;
     if (ev == EV_TOP) {
+      const int bin = exit_bin(c, p);
       const unsigned long long q = __float2ull_rn(__fmul_rn(p.W, kFix));
-      atomicAdd(smem + p.bin, q);
+      atomicAdd(smem + bin, q);
       atomicAdd(smem + nb + 1 + p.k, q);
       if (p.n_coll == 1u) atomicAdd(smem + nb + 1 + c.K, q);
       if (s.want_sumsq)
-        atomicAdd(smem + nb + 6 + c.K + p.bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
+        atomicAdd(smem + nb + 6 + c.K + bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
     } else if (ev == EV_BOTTOM) {
       atomicAdd(smem + nb + 2 + c.K, __float2ull_rn(__fmul_rn(p.W, kFix)));
     } else if (ev == EV_TRUNC) {

@@ -175,22 +175,27 @@ def test_inverse_fit_recovers_albedo(api):
     mt = api.Media.from_inputs(truth)
     tgt = api.walk(mt, o)
     tR, tB = tgt["R"].clone(), tgt["bins"].clone()
-    alpha0 = torch.clamp(mt.alpha + 0.08 * torch.sign(torch.randn_like(mt.alpha)), 0.3, 0.999)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    sign = torch.sign(torch.randn(mt.alpha.shape, device="cuda", generator=gen))
+    alpha0 = torch.clamp(mt.alpha + 0.08 * sign, 0.3, 0.999)
     logit = torch.logit(alpha0).clone().requires_grad_(True)
+    iters = 150
     opt = torch.optim.Adam([logit], lr=0.05)
+    sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, iters)
     err0 = None
-    for it in range(60):
+    for it in range(iters):
         a = torch.sigmoid(logit)
         R, bins, _ = api.SSSWalk.apply(a, mt.sigma_t, mt.g, mt.w, mt, o)
         loss = ((R - tR) ** 2).sum() + ((bins - tB) ** 2).sum()
         opt.zero_grad()
         loss.backward()
         opt.step()
+        sched.step()
         if err0 is None:
             err0 = float(loss)
     final = float(loss)
     print("inverse fit loss", err0, "->", final)
-    assert final < 0.05 * err0
+    assert final < 0.01 * err0
     # albedo of the heaviest medium per band is recovered where it matters
     a = torch.sigmoid(logit).detach()
     heavy = mt.w.argmax(0)
