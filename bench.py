@@ -134,6 +134,68 @@ def cpu_baseline_sample(n_texels=24):
                       f"spectral workload, FP64, {dt:.1f} s"}
 
 
+def run_pipeline(args):
+    """RGB texture -> decoder -> walk, timed end to end on the GPU, with the
+    error against the FP64 oracle pipeline on a 32 x 32 texel subset."""
+    import torch
+    import oracle
+    from oracle import decoder as dec_ref
+    from paper_2606_27604_b300 import api, inputs
+    side = args.pipeline_side
+    T = side * side
+    dev = torch.device("cuda", 0)
+    rgb_np = inputs.rgb_texture(side=side, seed=4)
+    W = inputs.decoder_weights(seed=4)
+    rgb = torch.from_numpy(rgb_np).to(dev)
+    packed = api.decoder_pack(W, device=dev)
+    dws = torch.empty(api.lib.sss_decode_workspace_size(T), dtype=torch.uint8, device=dev)
+    prm = {k: torch.empty(3, 81 * T, dtype=torch.float32, device=dev)
+           for k in ("alpha", "g", "sigma_t", "w")}
+    o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1004)
+    m = api.Media(prm["alpha"], prm["sigma_t"], prm["g"], prm["w"], None, 1024, None, 1.4)
+    wsp = api.alloc_workspace(m, o)
+    out = api.alloc_tallies(m, o)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        api.decode(rgb, packed, workspace=dws, out=prm)
+        api.walk(m, o, workspace=wsp, out=out)
+
+    step()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    api.decode(rgb, packed, workspace=dws, out=prm)
+    e[1].record(stream)
+    api.walk(m, o, workspace=wsp, out=out)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    t_dec, t_walk = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+    # oracle pipeline on the first 32 x 32 texels (rows of the texture)
+    sub = 32 * 32
+    ref = dec_ref.decode(rgb_np[:sub], W, bf16_activations=True)
+    Tb = sub
+    ids = (np.arange(81)[:, None] * T + np.arange(sub)[None, :]).reshape(-1)
+    refw = oracle.walk(ref["alpha"].astype(np.float32), ref["sigma_t"].astype(np.float32),
+                       ref["g"].astype(np.float32), ref["w"].astype(np.float32),
+                       np.full(81 * Tb, 1024, np.uint32), None, 1.4,
+                       oracle.OracleOpts(nbins=64, r_max_mm=10.0, seed=1004), inst_ids=ids)
+    R = out["R"].cpu().numpy()[ids]
+    se = np.sqrt(refw["se_R"] ** 2 + out["stderr_R"].cpu().numpy()[ids] ** 2)
+    z = (R - refw["R"]) / np.maximum(se, 1e-12)
+    paths = 81.0 * T * 1024
+    line = {"metric": "full pipeline RGB -> decoder -> walk", "workload":
+            f"{side}x{side} RGB, 81 bands, 1024 paths, 64 bins, n=1.4",
+            "decode_ms": t_dec * 1e3, "walk_ms": t_walk * 1e3,
+            "total_ms": (t_dec + t_walk) * 1e3, "paths_per_s": paths / (t_dec + t_walk),
+            "subset": "32x32 texels x 81 bands vs FP64 oracle decoder + oracle walk",
+            "R_z_abs_max": float(np.abs(z).max()), "R_z_rms": float(np.sqrt((z ** 2).mean())),
+            "R_rel_err_median": float(np.median(np.abs(R - refw["R"]) / refw["R"])),
+            "frac_within_4sigma": float((np.abs(z) <= 4).mean())}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -171,6 +233,9 @@ def main():
     ap.add_argument("--no-baselines", action="store_true",
                     help="skip the uneven-batch and plain one-launch-per-instance timings")
     ap.add_argument("--no-decoder", action="store_true")
+    ap.add_argument("--pipeline", action="store_true",
+                    help="run the full RGB -> decoder -> walk pipeline instead")
+    ap.add_argument("--pipeline-side", type=int, default=1024)
     ap.add_argument("--autotune", action="store_true",
                     help="pick the walk kernel's launch shape with the autotuner first")
     ap.add_argument("--texels", type=int, default=WORKLOAD["texels"],
@@ -182,6 +247,8 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.pipeline:
+        return run_pipeline(args)
 
     import torch
     ws, rank, local = _dist()

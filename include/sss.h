@@ -113,7 +113,11 @@ typedef struct {
  *                     (cached per argument set) and replay it.
  *   block_threads, unit_paths, regroup : launch shape of the persistent
  *                     kernel (0 = built-in defaults); results do not depend
- *                     on them. */
+ *                     on them.
+ *   instance_offset : number added to each instance's index in the random-
+ *                     number counters, so a shard [b, e) of a larger batch,
+ *                     walked with instance_offset = b, reproduces that
+ *                     batch's instances bit for bit (multi-GPU sharding). */
 typedef struct {
   int32_t nbins;
   float r_max_mm;
@@ -129,6 +133,7 @@ typedef struct {
   int32_t block_threads;
   int32_t unit_paths;
   int32_t regroup;
+  uint32_t instance_offset;
 } sss_walk_opts;
 
 /* Forward outputs, all float64 device arrays owned by the caller; any may be

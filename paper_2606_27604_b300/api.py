@@ -42,7 +42,7 @@ class Opts(C.Structure):
                 ("max_steps", C.c_uint32), ("seed", C.c_uint64), ("path_offset", C.c_uint32),
                 ("want_sumsq", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("block_threads", C.c_int32), ("unit_paths", C.c_int32),
-                ("regroup", C.c_int32)]
+                ("regroup", C.c_int32), ("instance_offset", C.c_uint32)]
 
 
 class Tallies(C.Structure):
@@ -129,6 +129,7 @@ class WalkOptions:
     block_threads: int = 0
     unit_paths: int = 0
     regroup: int = 0
+    instance_offset: int = 0
 
     def c(self) -> Opts:
         return Opts(**asdict(self))

@@ -135,6 +135,11 @@ WalkConst make_const(const sss_params* p, const sss_walk_opts* o) {
   c.key0 = (uint32_t)(o->seed & 0xffffffffull);
   c.key1 = (uint32_t)(o->seed >> 32);
   c.path_offset = o->path_offset;
+  c.inst_offset = o->instance_offset;
+  for (int r = 0; r < 10; ++r) {
+    c.rk[2 * r] = c.key0 + (uint32_t)r * 0x9E3779B9u;
+    c.rk[2 * r + 1] = c.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   return c;
 }
 
@@ -297,6 +302,8 @@ sss_status run(bool adj, const sss_params* p, const sss_walk_opts* o, void* ws, 
                sss_tallies* out, const sss_grad_in* gin, sss_grad_out* gout,
                sss_stream_t stream) {
   if (!params_ok(p) || !opts_ok(o)) return SSS_ERR_INVALID_ARG;
+  if ((uint64_t)o->instance_offset + (uint64_t)p->n_inst > 0x100000000ull)
+    return SSS_ERR_INVALID_ARG;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1))) return SSS_ERR_INVALID_ARG;
   if (adj && !gout) return SSS_ERR_INVALID_ARG;
   const Layout L = make_layout(p, o, adj);

@@ -40,6 +40,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The same block with the key schedule precomputed: rk[2r], rk[2r+1] are the
+// round-r keys (k0 + r W0, k1 + r W1).  With rk in the kernel's parameter
+// (constant) bank the XORs read it directly, so the key additions vanish.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+  }
+  return c;
+}
+
 // 23 random bits k -> (k + 1/2) * 2^-23, exact in binary32, strictly in (0,1).
 // The bits become the mantissa of 1 + k 2^-23 in [1, 2); subtracting
 // 1 - 2^-24 (exact: both operands lie in [1/2, 2]) leaves (k + 1/2) 2^-23.
@@ -68,6 +83,8 @@ struct WalkConst {
   uint32_t max_steps;
   uint32_t key0, key1;
   uint32_t path_offset;
+  uint32_t rk[20];   // Philox round keys derived from (key0, key1)
+  uint32_t inst_offset;  // added to the instance index in the counters
 };
 
 enum Event : int { EV_CONTINUE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_DEAD = 3, EV_TRUNC = 4 };
@@ -78,6 +95,7 @@ struct Path {
   float Aacc;     // weight deposited by collisions
   float alpha, sigt, fl, g, d;  // fl = ln(2) / sigma_t (flight scale for log2)
   uint32_t step, path, inst, n_coll;
+  uint32_t cinst;  // instance number in the random-number counters
   int k;
   float L;        // path length inside the medium (adjoint)
   float G;        // sum of d log p_HG / d g (adjoint)
@@ -107,7 +125,7 @@ __device__ __forceinline__ int select_medium(const WalkConst& c, uint32_t inst, 
 
 __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uint32_t path,
                                           float d, Path& p) {
-  const uint4 r = philox4x32_10(make_uint4(0u, path, inst, 1u), c.key0, c.key1);
+  const uint4 r = philox4x32_10_rk(make_uint4(0u, path, inst + c.inst_offset, 1u), c.rk);
   const int k = select_medium(c, inst, u23(r.x));
   const size_t off = (size_t)k * c.n_inst + inst;
   p.k = k;
@@ -123,6 +141,7 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.step = 0u;
   p.path = path;
   p.inst = inst;
+  p.cinst = inst + c.inst_offset;
   p.n_coll = 0u;
   p.L = 0.0f;
   p.G = 0.0f;
@@ -190,7 +209,7 @@ __device__ __forceinline__ float hg_dlogp_dg(float g, float mu) {
 template <bool ADJ>
 __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
   if (p.step >= c.max_steps) return EV_TRUNC;
-  const uint4 r = philox4x32_10(make_uint4(p.step, p.path, p.inst, 0u), c.key0, c.key1);
+  const uint4 r = philox4x32_10_rk(make_uint4(p.step, p.path, p.cinst, 0u), c.rk);
   p.step++;
   const float u0 = u23(r.x), u1 = u23(r.y), u2 = u23(r.z), u3 = u23(r.w);
 

@@ -179,6 +179,22 @@ def test_split_path_ranges_add_up_exactly(api):
     np.testing.assert_array_equal(full["raw"], ra["raw"] + rb["raw"])
 
 
+def test_instance_shards_reproduce_the_batch(api):
+    # two ranks' shards, walked with their instance offsets, concatenate to
+    # the whole batch bit for bit (no exchange during the walk)
+    from paper_2606_27604_b300.shard import shard_range
+    x = inputs.uneven_batch(n_inst=301, param_seed=8, log2_min=8, log2_max=12)
+    full, _, _ = run_gpu(x, opts(api, seed=44), raw=True)
+    parts = []
+    for r in range(2):
+        b, e = shard_range(x.n_inst, r, 2)
+        g, code, _ = run_gpu(x.subset(np.arange(b, e)), opts(api, seed=44, instance_offset=b),
+                             raw=True)
+        assert code == 0
+        parts.append(g["raw"])
+    np.testing.assert_array_equal(full["raw"], np.concatenate(parts, axis=0))
+
+
 def test_three_identical_media_equal_one(api):
     x = inputs.spectral_field(n_texels=3, param_seed=4, n_paths=4000)
     x3 = x.subset(np.arange(x.n_inst))
