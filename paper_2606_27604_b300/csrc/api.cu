@@ -183,9 +183,9 @@ sss_status persistent_shape(bool adj, const sss_params* p, const sss_walk_opts* 
                             int sms, Shape* sh) {
   constexpr size_t kSmemLimit = 200 * 1024;
   sh->block = o->block_threads ? o->block_threads : 256;
-  sh->regroup = o->regroup ? o->regroup : 8;
+  sh->regroup = o->regroup ? o->regroup : 6;
   sh->burst = 1;
-  sh->unit_paths = o->unit_paths ? (uint32_t)o->unit_paths : 1024u;
+  sh->unit_paths = o->unit_paths ? (uint32_t)o->unit_paths : 2048u;
   // two slots of accumulators per warp; shrink the block for wide histograms
   const size_t per_warp = (size_t)2 * acc_words * 8 + 2 * 32;  // + two 32-byte slot headers
   if (per_warp > kSmemLimit) return SSS_ERR_INVALID_ARG;

@@ -157,21 +157,115 @@ __device__ __forceinline__ float activate(float x, int act) {
   return act == ACT_TANH ? tanh_fast(x) : act == ACT_SIGMOID ? sigmoid_fast(x) : x;
 }
 
-template <int BN>
+template <int COLS>
 struct TmemCols {
-  static constexpr int value = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  // TMEM allocations are powers of two >= 32 columns
+  static constexpr int value2 = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128
+                              : COLS <= 256 ? 256 : 512;
 };
 
+// ------------------------------------------------------------- epilogues --
+// Hidden layer: bias, activation, BF16 store of one 16-column chunk.
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a -> low half
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void epi_hidden_chunk(const float* v, int row, int col,
+                                                 const float* sbias, const EpiParams& ep) {
+  if (row >= ep.M || col >= ep.n_valid) return;
+  uint32_t w[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    w[j] = pack_bf16x2(activate(v[2 * j] + sbias[col + 2 * j], ep.act),
+                       activate(v[2 * j + 1] + sbias[col + 2 * j + 1], ep.act));
+  __nv_bfloat16* dst = ep.out + (size_t)row * ep.ldc + ep.col0 + col;
+  if (col + 16 <= ep.n_valid && ((ep.col0 + col) & 7) == 0 && (ep.ldc & 7) == 0) {
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  } else {
+    uint16_t* d16 = reinterpret_cast<uint16_t*>(dst);
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (col + j < ep.n_valid) d16[j] = (uint16_t)(w[j >> 1] >> ((j & 1) * 16));
+  }
+}
+
+// Dec_T's last layer, one group of 36 columns = 3 source bands x (K = 3
+// media x 4 channels): the source band of even visible band 2P and the two
+// source bands halfway around odd visible band 2P+1.  Channels: alpha, g,
+// sigma_t (sigmoid; sigma_t = 10^(3 s)), w (softmax over the media).
+__device__ __forceinline__ void epi_final_group(const float* v, int row, int P,
+                                                const float* bp, const EpiParams& ep) {
+  if (row >= ep.M || P >= ep.n_pairs) return;
+  float a[3][3], gg[3][3], st[3][3], ww[3][3];  // [slot][k]
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    float m = -3.0e38f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int c = sl * 12 + k * 4;
+      a[sl][k] = sigmoid_fast(v[c + 0] + bp[c + 0]);
+      gg[sl][k] = sigmoid_fast(v[c + 1] + bp[c + 1]);
+      st[sl][k] = exp2f(3.0f * 3.3219280948873623f * sigmoid_fast(v[c + 2] + bp[c + 2]));
+      ww[sl][k] = v[c + 3] + bp[c + 3];
+      m = fmaxf(m, ww[sl][k]);
+    }
+    float z = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ww[sl][k] = __expf(ww[sl][k] - m);
+      z += ww[sl][k];
+    }
+    const float iz = __fdividef(1.0f, z);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ww[sl][k] *= iz;
+  }
+  const size_t T = (size_t)ep.T;
+  const size_t nin = T * (size_t)ep.n_dst;
+  const int je = 2 * P;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const size_t o = (size_t)k * nin + (size_t)je * T + row;
+    ep.alpha[o] = a[0][k];
+    ep.g[o] = gg[0][k];
+    ep.sigma_t[o] = st[0][k];
+    ep.w[o] = ww[0][k];
+  }
+  if (je + 1 < ep.n_dst) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const size_t o = (size_t)k * nin + (size_t)(je + 1) * T + row;
+      ep.alpha[o] = 0.5f * (a[1][k] + a[2][k]);
+      ep.g[o] = 0.5f * (gg[1][k] + gg[2][k]);
+      ep.sigma_t[o] = 0.5f * (st[1][k] + st[2][k]);
+      ep.w[o] = 0.5f * (ww[1][k] + ww[2][k]);
+    }
+  }
+}
+
 // ------------------------------------------------------------- the GEMM --
+// Persistent: one CTA per SM walks the output tiles (n fastest, so the CTAs
+// working at one time share rows of A in L2).  Warp 0 streams A/B k-blocks
+// through the shared-memory ring without stopping between tiles; warp 1
+// issues the MMAs into one of two TMEM accumulators; warps 2..9 drain the
+// other accumulator (two warps per TMEM lane quarter, alternate 16-column
+// chunks), so a tile's epilogue overlaps the next tile's MMAs.  The bias
+// vector is staged once in shared memory.
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+
 template <int BN, int EPI>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
 gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                  const __grid_constant__ CUtensorMap tmap_b, int a_x0, int num_kb,
-                 const float* __restrict__ bias, EpiParams ep, unsigned int* status) {
+                 int n_tiles, long long m_tiles, const float* __restrict__ bias, EpiParams ep,
+                 unsigned int* status) {
   constexpr int A_BYTES = BM * BK * 2;
   constexpr int B_BYTES = BN * BK * 2;
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  constexpr int TCOLS = TmemCols<BN>::value;
+  constexpr int TCOLS = TmemCols<2 * BN>::value2;
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
   static_assert(B_BYTES % 1024 == 0, "tiles must stay 1024-byte aligned");
 
@@ -180,20 +274,26 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                                              ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* tfull = empty + STAGES;   // accumulator b ready for the epilogue
+  uint64_t* tempty = tfull + 2;       // accumulator b drained by the epilogue
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile uint32_t* abort_flag = tmem_slot + 1;
+  float* sbias = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int n_tile = blockIdx.x;
-  const int m_tile = blockIdx.y;
+  const long long total = m_tiles * (long long)n_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kEpiWarps);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -204,6 +304,7 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  for (int j = threadIdx.x; j < n_tiles * BN; j += blockDim.x) sbias[j] = bias[j];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -215,129 +316,110 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                    : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap_b))
                    : "memory");
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u)) {
-          atomicOr(status, DEC_FLAG_TIMEOUT);
-          break;
+      long long it = 0;
+      for (long long t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+        const int m_tile = (int)(t / n_tiles), n_tile = (int)(t % n_tiles);
+        for (int kb = 0; kb < num_kb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u)) {
+            atomicOr(status, DEC_FLAG_TIMEOUT);
+            *abort_flag = 1u;
+            break;
+          }
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          uint8_t* sa = smem + s * STAGE_BYTES;
+          tma_load_2d(sa, &tmap_a, a_x0 + kb * BK, m_tile * BM, &full[s]);
+          tma_load_2d(sa + A_BYTES, &tmap_b, kb * BK, n_tile * BN, &full[s]);
         }
-        mbar_expect_tx(&full[s], STAGE_BYTES);
-        uint8_t* sa = smem + s * STAGE_BYTES;
-        tma_load_2d(sa, &tmap_a, a_x0 + kb * BK, m_tile * BM, &full[s]);
-        tma_load_2d(sa + A_BYTES, &tmap_b, kb * BK, n_tile * BN, &full[s]);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16<BN>();
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(&full[s], ph)) {
+      long long it = 0;
+      int i = 0;
+      for (long long t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++i) {
+        const int b = i & 1;
+        if (!mbar_wait(&tempty[b], ((uint32_t)(i >> 1) & 1u) ^ 1u)) {
           atomicOr(status, DEC_FLAG_TIMEOUT);
+          *abort_flag = 1u;
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t b0 = a0 + A_BYTES;
-        const uint64_t da = smem_desc_sw128(a0), db = smem_desc_sw128(b0);
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        for (int kb = 0; kb < num_kb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph)) {
+            atomicOr(status, DEC_FLAG_TIMEOUT);
+            *abort_flag = 1u;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+          const uint64_t da = smem_desc_sw128(a0), db = smem_desc_sw128(a0 + A_BYTES);
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k)  // K = 16 per MMA: advance 32 bytes
-          umma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
-        umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+          for (int k = 0; k < BK / 16; ++k)  // K = 16 per MMA: advance 32 bytes
+            umma_bf16(acc, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+          umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+        }
+        umma_commit(&tfull[b]);    // accumulator b complete
       }
-      umma_commit(done);
     }
   } else {
-    // ---------------------------- epilogue: warps 2..5 -------------------
-    const int q = warp & 3;  // TMEM lane quarter this warp may read
-    const int row = m_tile * BM + q * 32 + lane;
-    const bool wait_ok = mbar_wait(done, 0u);
-    if (!wait_ok && lane == 0) atomicOr(status, DEC_FLAG_TIMEOUT);
-    tc_fence_after();
-    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
-    if (EPI == EPI_HIDDEN) {
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tmem_ld16(taddr + c0, v);
-        tmem_wait_ld();
-        const int col = n_tile * BN + c0;
-        if (!wait_ok || row >= ep.M || col >= ep.n_valid) continue;
-        __nv_bfloat16 h[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float b = (col + j < ep.n_valid) ? __ldg(bias + col + j) : 0.0f;
-          h[j] = __float2bfloat16_rn(activate(v[j] + b, ep.act));
-        }
-        __nv_bfloat16* dst = ep.out + (size_t)row * ep.ldc + ep.col0 + col;
-        if (col + 16 <= ep.n_valid && ((ep.col0 + col) & 7) == 0 && (ep.ldc & 7) == 0) {
-          const uint4* src = reinterpret_cast<const uint4*>(h);
-          reinterpret_cast<uint4*>(dst)[0] = src[0];
-          reinterpret_cast<uint4*>(dst)[1] = src[1];
-        } else {
-          for (int j = 0; j < 16 && col + j < ep.n_valid; ++j) dst[j] = h[j];
-        }
+    // ---------------------------- epilogue: warps 2..9 -------------------
+    const int q = warp & 3;          // TMEM lane quarter this warp may read
+    const int half = (warp - 2) >> 2;  // which alternate column chunks
+    int i = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      const int m_tile = (int)(t / n_tiles), n_tile = (int)(t % n_tiles);
+      const int b = i & 1;
+      const bool ok = mbar_wait(&tfull[b], (uint32_t)(i >> 1) & 1u);
+      if (!ok) {
+        if (lane == 0) atomicOr(status, DEC_FLAG_TIMEOUT);
+        *abort_flag = 1u;
+        break;
       }
-    } else {
-      // Dec_T's last layer.  Columns come in groups of 36 = 3 source bands x
-      // (K = 3 media x 4 channels): group P holds the source band of the
-      // even target band 2P and the two source bands halfway around the odd
-      // target band 2P+1.  Channels: alpha, g, sigma_t (sigmoid), w (softmax
-      // over the media).
-      for (int gq = 0; gq < BN / 36; ++gq) {
-        float v[36];
-        tmem_ld16(taddr + gq * 36, v);
-        tmem_ld16(taddr + gq * 36 + 16, v + 16);
-        tmem_ld4(taddr + gq * 36 + 32, v + 32);
+      tc_fence_after();
+      const int row = m_tile * BM + q * 32 + lane;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+      if (EPI == EPI_HIDDEN) {
+        // read this warp's chunks of the accumulator row, release TMEM, then
+        // finish the math and the stores
+        constexpr int NCH = BN / 16;
+        constexpr int MY = (NCH + 1) / 2;
+        float v[MY * 16];
+#pragma unroll
+        for (int j = 0; j < MY; ++j) {
+          const int ch = 2 * j + half;
+          if (ch < NCH) tmem_ld16(taddr + ch * 16, v + j * 16);
+        }
         tmem_wait_ld();
-        const int P = n_tile * (BN / 36) + gq;
-        if (!wait_ok || row >= ep.M || P >= ep.n_pairs) continue;
-        const float* bp = bias + (size_t)(n_tile * BN + gq * 36);
-        float a[3][3], gg[3][3], st[3][3], ww[3][3];  // [slot][k]
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                        smem_u32(&tempty[b]))
+                                    : "memory");
 #pragma unroll
-        for (int sl = 0; sl < 3; ++sl) {
-          float m = -3.0e38f;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int c = sl * 12 + k * 4;
-            a[sl][k] = sigmoid_fast(v[c + 0] + __ldg(bp + c + 0));
-            gg[sl][k] = sigmoid_fast(v[c + 1] + __ldg(bp + c + 1));
-            st[sl][k] = exp2f(3.0f * 3.3219280948873623f * sigmoid_fast(v[c + 2] + __ldg(bp + c + 2)));
-            ww[sl][k] = v[c + 3] + __ldg(bp + c + 3);
-            m = fmaxf(m, ww[sl][k]);
-          }
-          float z = 0.0f;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            ww[sl][k] = __expf(ww[sl][k] - m);
-            z += ww[sl][k];
-          }
-          const float iz = __fdividef(1.0f, z);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) ww[sl][k] *= iz;
+        for (int j = 0; j < MY; ++j) {
+          const int ch = 2 * j + half;
+          if (ch < NCH) epi_hidden_chunk(v + j * 16, row, n_tile * BN + ch * 16, sbias, ep);
         }
-        const size_t T = (size_t)ep.T;
-        const size_t nin = T * (size_t)ep.n_dst;
-        const int je = 2 * P;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const size_t o = (size_t)k * nin + (size_t)je * T + row;
-          ep.alpha[o] = a[0][k];
-          ep.g[o] = gg[0][k];
-          ep.sigma_t[o] = st[0][k];
-          ep.w[o] = ww[0][k];
+      } else {
+        for (int gq = half; gq < BN / 36; gq += 2) {
+          float v[36];
+          tmem_ld16(taddr + gq * 36, v);
+          tmem_ld16(taddr + gq * 36 + 16, v + 16);
+          tmem_ld4(taddr + gq * 36 + 32, v + 32);
+          tmem_wait_ld();
+          epi_final_group(v, row, n_tile * (BN / 36) + gq, sbias + n_tile * BN + gq * 36, ep);
         }
-        if (je + 1 < ep.n_dst) {
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const size_t o = (size_t)k * nin + (size_t)(je + 1) * T + row;
-            ep.alpha[o] = 0.5f * (a[1][k] + a[2][k]);
-            ep.g[o] = 0.5f * (gg[1][k] + gg[2][k]);
-            ep.sigma_t[o] = 0.5f * (st[1][k] + st[2][k]);
-            ep.w[o] = 0.5f * (ww[1][k] + ww[2][k]);
-          }
-        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                        smem_u32(&tempty[b]))
+                                    : "memory");
       }
     }
   }
@@ -402,12 +484,21 @@ template <int BN, int EPI>
 static cudaError_t launch_gemm_t(const CUtensorMap& ta, const CUtensorMap& tb, int a_x0,
                                  int num_kb, int n_tiles, long long m_tiles, const float* bias,
                                  const EpiParams& ep, unsigned int* status, cudaStream_t st) {
-  constexpr size_t smem = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 + 256;
+  // at least half of the SM's shared memory, so exactly one CTA (and one
+  // TMEM allocation of up to 512 columns) per SM
+  constexpr size_t ring = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2);
+  const size_t smem = (ring > 120 * 1024 ? ring : 120 * 1024) + 1024 + 256 +
+                      (size_t)n_tiles * BN * sizeof(float);
   auto fn = gemm_bf16_kernel<BN, EPI>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)n_tiles, (unsigned)m_tiles);
-  fn<<<grid, 192, smem, st>>>(ta, tb, a_x0, num_kb, bias, ep, status);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long total = (long long)n_tiles * m_tiles;
+  const unsigned grid = (unsigned)(total < sms ? total : sms);
+  if (grid == 0) return cudaSuccess;
+  fn<<<grid, kThreads, smem, st>>>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status);
   return cudaGetLastError();
 }
 

@@ -190,14 +190,14 @@ sss_status sss_decode(const float* rgb, int64_t T, const void* packed, void* wor
   // enc1..dec_t2: hidden layers; dec_t3: the parameter epilogue.
   // X0 is [T][256] in BUF_R1 (row pitch 256), X1 likewise in BUF_R2.
   const Step steps[9] = {
-      {X0, 256, 0, 1, 128, EPI_HIDDEN, X1, 256, 0, 256, ACT_TANH},
+      {X0, 256, 0, 1, 256, EPI_HIDDEN, X1, 256, 0, 256, ACT_TANH},
       {X1, 256, 0, 2, 16, EPI_HIDDEN, buf[BUF_T], 384, 376, 5, ACT_SIGMOID},
-      {buf[BUF_T], 384, 376, 3, 128, EPI_HIDDEN, buf[BUF_R1], 512, 0, 512, ACT_TANH},
-      {buf[BUF_R1], 512, 0, 4, 128, EPI_HIDDEN, buf[BUF_R2], 512, 0, 512, ACT_TANH},
+      {buf[BUF_T], 384, 376, 3, 256, EPI_HIDDEN, buf[BUF_R1], 512, 0, 512, ACT_TANH},
+      {buf[BUF_R1], 512, 0, 4, 256, EPI_HIDDEN, buf[BUF_R2], 512, 0, 512, ACT_TANH},
       {buf[BUF_R2], 512, 0, 5, 128, EPI_HIDDEN, buf[BUF_T], 384, 0, 376, ACT_SIGMOID},
-      {buf[BUF_T], 384, 0, 6, 128, EPI_HIDDEN, buf[BUF_A], 768, 0, 768, ACT_TANH},
-      {buf[BUF_A], 768, 0, 7, 128, EPI_HIDDEN, buf[BUF_B], 768, 0, 768, ACT_TANH},
-      {buf[BUF_B], 768, 0, 8, 128, EPI_HIDDEN, buf[BUF_A], 768, 0, 768, ACT_TANH},
+      {buf[BUF_T], 384, 0, 6, 256, EPI_HIDDEN, buf[BUF_A], 768, 0, 768, ACT_TANH},
+      {buf[BUF_A], 768, 0, 7, 256, EPI_HIDDEN, buf[BUF_B], 768, 0, 768, ACT_TANH},
+      {buf[BUF_B], 768, 0, 8, 256, EPI_HIDDEN, buf[BUF_A], 768, 0, 768, ACT_TANH},
       {buf[BUF_A], 768, 0, 9, kFinalBN, EPI_FINAL, nullptr, 0, 0, 0, ACT_NONE},
   };
   for (const Step& s : steps) {

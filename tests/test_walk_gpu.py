@@ -72,6 +72,25 @@ def test_single_wavelength_parity_and_closed_forms(api):
     assert np.all(g["truncated"] == 0)
 
 
+def test_independent_streams_agree_statistically(api):
+    # GPU and oracle on different seeds: agreement here cannot come from the
+    # shared random numbers.  Every R within 4 sigma; the 32 x 16 bins are
+    # many comparisons, so their largest |z| may reach 5 (P(|z|>5) ~ 6e-7).
+    x = inputs.single_wavelength(param_seed=0, n_paths=1 << 18)
+    x.n_rel = 1.4
+    g, code, _ = run_gpu(x, opts(api, nbins=32, r_max_mm=10.0, seed=777))
+    assert code == 0
+    r = run_oracle(x, opts(api, nbins=32, r_max_mm=10.0, seed=31337))
+    se = np.sqrt(g["stderr_R"] ** 2 + r["se_R"] ** 2)
+    z = (g["R"] - r["R"]) / se
+    print("R z-scores", np.round(z, 2))
+    assert np.all(np.abs(z) <= 4.0)
+    seb = np.sqrt(g["stderr_bins"] ** 2 + r["se_bins"] ** 2)
+    m = seb > 0
+    zb = (g["bins"] - r["bins"])[m] / seb[m]
+    assert np.abs(zb).max() <= 5.0 and np.mean(np.abs(zb) <= 4.0) >= 0.995
+
+
 def test_h_function_at_1e8_paths(api):
     # 2^27 paths per set: relative error <= 1e-3 and within 4 standard errors
     x = inputs.single_wavelength(param_seed=0, n_paths=1 << 27).subset(np.arange(10))
