@@ -44,6 +44,24 @@ DECODER_MACS_PER_TEXEL = (3 * 256 + 256 * 256 + 256 * 5) + (5 * 512 + 512 * 512 
     + (381 * 768 + 2 * 768 * 768 + 768 * 121 * 12)
 
 
+# DRAM traffic of the walk kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the 1024-texel case, scaled by 64 to the
+# 65536-texel launch (the traffic grows with the instances walked).  Valid
+# only while the kernel sources are the ones captured (sha1 below).
+WALK_TRAFFIC = {"bytes_per_launch": (61.306880e6 + 11.990528e6) * 64,
+                "source_sha1": "f1518523cafba9d86ee9d629bcb4d9f50ab2c2de",
+                "capture": "profiles/walk_persistent_spectral_field.md"}
+
+
+def _walk_source_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("walk_core.cuh", "walk_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2606_27604_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def _measured_peak(key, fallback):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -469,8 +487,11 @@ def main():
     peak = sms * SM_LANES_PER_CLK * f_mhz * 1e6 / 1e12
     achieved = total_draws * ALG_ALU_OPS_PER_STEP / kmean / 1e12
     mufu = total_draws * ALG_MUFU_OPS_PER_STEP / kmean / (sms * MUFU_LANES_PER_CLK * f_mhz * 1e6)
+    traffic = WALK_TRAFFIC["bytes_per_launch"] \
+        if _walk_source_sha1() == WALK_TRAFFIC["source_sha1"] and \
+        WORKLOAD["texels"] == 256 * 256 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "walk_persistent_kernel<false>",
                 "peak_basis": f"{sms} SMs x {SM_LANES_PER_CLK} FP32/INT32 lanes/clk x "
                               f"{f_mhz:.0f} MHz (median SM clock sampled in the timed region)",
