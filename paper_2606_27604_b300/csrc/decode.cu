@@ -442,20 +442,28 @@ enc0_kernel(const float* __restrict__ rgb, long long T, const __nv_bfloat16* __r
   for (int i = threadIdx.x; i < 256 * 4; i += blockDim.x)
     sw[i] = i < 768 ? __bfloat162float(W[i]) : b[i - 768];
   __syncthreads();
-  // one warp per texel row, each lane 8 outputs (16-byte store)
-  const long long rowg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // one warp per texel row, each lane 8 outputs (16-byte store); a grid of a
+  // few blocks per SM strides over the rows so the weights load once per block
   const int lane = threadIdx.x & 31;
-  if (rowg >= T) return;
-  const float r = rgb[rowg * 3 + 0], g = rgb[rowg * 3 + 1], bl = rgb[rowg * 3 + 2];
-  __nv_bfloat16 h[8];
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long rowg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; rowg < T;
+       rowg += warps) {
+    const float r = rgb[rowg * 3 + 0], g = rgb[rowg * 3 + 1], bl = rgb[rowg * 3 + 2];
+    uint32_t h[4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int o = lane * 8 + j;
-    const float z = __fmaf_rn(sw[o * 3 + 0], r,
-                              __fmaf_rn(sw[o * 3 + 1], g, __fmaf_rn(sw[o * 3 + 2], bl, sw[768 + o])));
-    h[j] = __float2bfloat16_rn(tanh_fast(z));
+    for (int j = 0; j < 4; ++j) {
+      float z2[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int o = lane * 8 + 2 * j + e;
+        z2[e] = tanh_fast(__fmaf_rn(sw[o * 3 + 0], r,
+                                    __fmaf_rn(sw[o * 3 + 1], g,
+                                              __fmaf_rn(sw[o * 3 + 2], bl, sw[768 + o]))));
+      }
+      h[j] = pack_bf16x2(z2[0], z2[1]);
+    }
+    reinterpret_cast<uint4*>(out + rowg * 256)[lane] = make_uint4(h[0], h[1], h[2], h[3]);
   }
-  reinterpret_cast<uint4*>(out + rowg * 256)[lane] = *reinterpret_cast<const uint4*>(h);
 }
 
 // --------------------------------------------------------------- packing --
@@ -520,8 +528,12 @@ cudaError_t launch_gemm(int bn, int epi, const CUtensorMap& ta, const CUtensorMa
 cudaError_t launch_enc0(const float* rgb, long long T, const __nv_bfloat16* W, const float* b,
                         __nv_bfloat16* out, cudaStream_t st) {
   if (T <= 0) return cudaSuccess;
-  const long long threads = T * 32;
-  enc0_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(rgb, T, W, b, out);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long need = (T * 32 + 255) / 256;
+  const long long grid = need < 8LL * sms ? need : 8LL * sms;
+  enc0_kernel<<<(unsigned)grid, 256, 0, st>>>(rgb, T, W, b, out);
   return cudaGetLastError();
 }
 

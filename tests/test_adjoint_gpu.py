@@ -202,3 +202,50 @@ def test_inverse_fit_recovers_albedo(api):
     idx = torch.arange(mt.n_inst, device="cuda")
     err = (a[heavy, idx] - mt.alpha[heavy, idx]).abs()
     assert float(err.median()) < 0.02
+
+
+def test_sigma_t_and_g_gradients_match_crn_finite_differences(api):
+    # 64 instances of the adjoint workload; central differences with common
+    # random numbers (same seed) at h = 1e-3, their error from 32 disjoint
+    # path ranges (path_offset), against the replay adjoint.  FD and adjoint
+    # are different estimators of the same derivative, so compare by z.  With
+    # 32 batch means z is t-distributed with 31 degrees of freedom: over the
+    # 256 comparisons max |z| <= 5 and mean z^2 <= 2 (expected 1.07).
+    import torch
+    x = inputs.spectral_field(n_texels=1, param_seed=3, n_paths=1 << 16).subset(np.arange(64))
+    N, B = 1 << 16, 32
+    o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1003)
+    gb = np.zeros((64, 64)); gb[:, 2] = 1.0
+    gR = np.ones(64)
+    adj, code, _ = _grads_gpu(api, x, o, grad_R=gR, grad_bins=gb)
+    assert code == 0
+    # per-instance standard error of the adjoint estimator from the oracle
+    xs = x.subset(np.arange(64)); xs.n_paths = np.full(64, N // B, np.uint32)
+    r = oracle.walk_grad(xs.alpha, xs.sigma_t, xs.g, xs.w, xs.n_paths, None, x.n_rel,
+                         to_oracle_opts(o), grad_R=gR, grad_bins=gb)
+    for param, key, rel in (("sigma_t", "d_sigma_t", True), ("g", "d_g", False)):
+        for k in (0, 1):
+            fds = []
+            for b in range(B):
+                ob = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1003, path_offset=b * (N // B))
+                vals = []
+                for sgn in (+1, -1):
+                    xp = x.subset(np.arange(64)); xp.n_paths = np.full(64, N // B, np.uint32)
+                    arr = getattr(xp, param)
+                    base = arr[k].astype(np.float64)
+                    h = 1e-3 * base if rel else np.full(64, 1e-3)
+                    arr[k] = (base + sgn * h).astype(np.float32)
+                    res = api.walk(api.Media.from_inputs(xp), ob)
+                    vals.append((res["R"] + res["bins"][:, 2]).cpu().numpy())
+                    step = getattr(xp, param)[k].astype(np.float64)
+                    if sgn == +1:
+                        up = step
+                    else:
+                        dn = step
+                fds.append((vals[0] - vals[1]) / (up - dn))
+            fds = np.array(fds)
+            fd, fd_se = fds.mean(0), fds.std(0, ddof=1) / np.sqrt(B)
+            se_adj = r["se_" + key][k] / np.sqrt(B)
+            z = (adj[key][k] - fd) / np.sqrt(fd_se ** 2 + se_adj ** 2)
+            print(param, k, "z rms", np.sqrt(np.mean(z ** 2)), "max", np.abs(z).max())
+            assert np.abs(z).max() <= 5.0 and np.mean(z ** 2) <= 2.0, (param, k)
