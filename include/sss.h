@@ -117,7 +117,13 @@ typedef struct {
  *   instance_offset : number added to each instance's index in the random-
  *                     number counters, so a shard [b, e) of a larger batch,
  *                     walked with instance_offset = b, reproduces that
- *                     batch's instances bit for bit (multi-GPU sharding). */
+ *                     batch's instances bit for bit (multi-GPU sharding).
+ *   incidence       : 0 = normal incidence at the origin (Eq. 3, default);
+ *                     1 = cosine-weighted incident lobe (the fitting
+ *                     illumination of Sec. 8): outside cosine sqrt(u),
+ *                     azimuth 2 pi u' from a third Philox draw per path
+ *                     (tag 2), refracted by Snell's law, entry weight 1 - F
+ *                     at the refracted angle when entry_fresnel = 1. */
 typedef struct {
   int32_t nbins;
   float r_max_mm;
@@ -134,6 +140,7 @@ typedef struct {
   int32_t unit_paths;
   int32_t regroup;
   uint32_t instance_offset;
+  int32_t incidence;
 } sss_walk_opts;
 
 /* Forward outputs, all float64 device arrays owned by the caller; any may be
@@ -282,6 +289,47 @@ size_t sss_decode_workspace_size(int64_t T);
 sss_status sss_decode(const float* rgb, int64_t T, const void* packed, void* workspace,
                       size_t workspace_bytes, float* alpha, float* g, float* sigma_t, float* w,
                       sss_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * LUT-based mixture fit (paper Sec. 4.2, Eq. 6-9).  Tables of a homogeneous
+ * semi-infinite medium at sigma_t = 1 (built with sss_walk, K = 1):
+ *   R  [na][ng]      total reflectance R(alpha_i, g_j)
+ *   p  [na][ng][nb]  radial exit density (per unit area, mfp^-2) at the bin
+ *                    centres rho_b = (b + 1/2) drho
+ * on alpha_i = a0 + i da, g_j = g0 + j dg (float32, device).  Lookups are
+ * bilinear in (alpha, g) and linear in rho, clamped to the grid; extinction
+ * rescales the radial axis: P(r | alpha, g, sigma_t) = sigma_t^2 p(sigma_t r).
+ * For each problem (tone x wavelength) the fit minimises
+ *   L = RMSE_j(log P_hat(r_j), log P_MC(r_j)) + lambda_R (R_hat - R_MC)^2,
+ *   R_hat = sum_k w_k R(alpha_k, g_k),  P_hat(r) = sum_k w_k P(r | theta_k),
+ * over the radii with P_MC > 0, by Adam (0.9, 0.999, 1e-8) with learning
+ * rate lr (1 + cos(pi (t-1) / steps)) / 2.  Raw parameters per problem,
+ * [4K] float32, in/out: [alpha_raw K][g_raw K][log sigma_t K][w_raw K] with
+ * alpha = a_lo + (a_hi - a_lo) sigmoid(raw), g likewise, sigma_t = exp(raw),
+ * w = softmax(raw).  One warp per problem. */
+typedef struct {
+  const float* R;
+  const float* p;
+  int32_t na, ng, nb;
+  float a0, da, g0, dg, drho;
+} sss_lut;
+
+typedef struct {
+  int32_t K;        /* media, 1..4 */
+  int32_t steps;    /* Adam steps (0: only evaluate loss and gradient) */
+  float lr;         /* 1e-2 in the paper */
+  float lambda_R;   /* 5 in the paper */
+  float a_lo, a_hi, g_lo, g_hi;
+} sss_fit_opts;
+
+/* r_mm [n_r] radii (mm, n_r <= 64), P_mc [n_prob][n_r] target profile
+ * densities (mm^-2; entries <= 0 are ignored), R_mc [n_prob] target
+ * reflectances, raw [n_prob][4K] in/out, loss [n_prob] out (may be NULL),
+ * grad [n_prob][4K] out: gradient at the returned parameters (may be NULL).
+ * All device pointers. */
+sss_status sss_lut_fit(const sss_lut* lut, int64_t n_prob, const float* r_mm, int32_t n_r,
+                       const float* P_mc, const float* R_mc, const sss_fit_opts* o, float* raw,
+                       float* loss, float* grad, sss_stream_t stream);
 
 /* Profiling hook.  With both events non-NULL (cudaEvent_t handles created by
  * the caller), each following sss_walk / sss_walk_bwd issued from this host

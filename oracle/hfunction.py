@@ -62,3 +62,10 @@ def reflectance_single(alpha: float) -> float:
 def reflectance_total_dalpha(alpha: float, h: float = 1e-6, n: int = 400) -> float:
     """dR/dalpha by a central difference of the closed form."""
     return (reflectance_total(alpha + h, n=n) - reflectance_total(alpha - h, n=n)) / (2 * h)
+
+
+def reflectance_cosine_lobe(alpha: float, n: int = 400) -> float:
+    """Diffuse reflectance under a cosine-weighted incident lobe,
+    2 int_0^1 R(mu) mu dmu = 1 - 2 sqrt(1 - alpha) int_0^1 H(mu) mu dmu."""
+    mu, wq, H = h_nodes(alpha, n)
+    return float(1.0 - 2.0 * np.sqrt(1.0 - alpha) * (wq * H * mu).sum())

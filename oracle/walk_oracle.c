@@ -176,9 +176,10 @@ typedef struct {
   double r_max_mm;
   int mode;            /* 0 = albedo weighting + Russian roulette, 1 = analog */
   double rr_threshold; /* W_th; 0 disables roulette (weight mode only) */
-  int entry_fresnel;   /* 1: entry weight 1-R0 (specular excluded) */
+  int entry_fresnel;   /* 1: entry weight 1 - F (specular excluded) */
   uint32_t max_steps;
   uint64_t seed;
+  int incidence;       /* 0 = normal, 1 = cosine-weighted lobe */
 } oracle_opts;
 
 typedef struct {
@@ -213,12 +214,25 @@ void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
   double st = sigma_t[(int64_t)k * n_inst + inst];
   double gg = g[(int64_t)k * n_inst + inst];
 
-  /* Normal incidence at the origin (Eq. 3); weight after the entry BTDF. */
-  double R0 = (n_rel - 1.0) / (n_rel + 1.0);
-  R0 *= R0;
-  double W = o->entry_fresnel ? 1.0 - R0 : 1.0;
+  /* Entry at the origin.  Normal incidence (Eq. 3), or a cosine-weighted
+   * incident lobe (the fitting assumption of Sec. 8): outside cosine
+   * sqrt(u), azimuth 2 pi u', refracted into the medium by Snell's law.
+   * The weight after the entry BTDF is 1 - F at the refracted angle (the
+   * reflectance is the same from either side). */
   double pos[3] = {0.0, 0.0, 0.0};
   double dir[3] = {0.0, 0.0, 1.0};
+  if (o->incidence == 1) {
+    double v[4];
+    draw4(o->seed, 0u, path, rng_inst, 2u, v);
+    const double mu_o = sqrt(v[0]);
+    const double sin_o = sqrt(fmax(0.0, 1.0 - mu_o * mu_o));
+    const double sin_i = sin_o / n_rel;
+    const double phi = 2.0 * M_PI * v[1];
+    dir[0] = sin_i * cos(phi);
+    dir[1] = sin_i * sin(phi);
+    dir[2] = sqrt(1.0 - sin_i * sin_i);
+  }
+  double W = o->entry_fresnel ? 1.0 - oracle_fresnel(dir[2], n_rel) : 1.0;
   double d = thickness_mm; /* +inf: semi-infinite */
 
   uint32_t step = 0;

@@ -42,7 +42,8 @@ class Opts(C.Structure):
                 ("max_steps", C.c_uint32), ("seed", C.c_uint64), ("path_offset", C.c_uint32),
                 ("want_sumsq", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("block_threads", C.c_int32), ("unit_paths", C.c_int32),
-                ("regroup", C.c_int32), ("instance_offset", C.c_uint32)]
+                ("regroup", C.c_int32), ("instance_offset", C.c_uint32),
+                ("incidence", C.c_int32)]
 
 
 class Tallies(C.Structure):
@@ -130,6 +131,7 @@ class WalkOptions:
     unit_paths: int = 0
     regroup: int = 0
     instance_offset: int = 0
+    incidence: int = 0
 
     def c(self) -> Opts:
         return Opts(**asdict(self))
@@ -400,3 +402,41 @@ def walk_noalloc(m: Media, o: WalkOptions, out: dict, stream=None):
     code = lib.sss_walk_noalloc(C.byref(p), C.byref(oc), C.byref(t), C.byref(flags),
                                 _stream(stream))
     return code, flags.value
+
+
+# --------------------------------------------------------------- LUT fit --
+class Lut(C.Structure):
+    _fields_ = [("R", C.c_void_p), ("p", C.c_void_p), ("na", C.c_int32), ("ng", C.c_int32),
+                ("nb", C.c_int32), ("a0", C.c_float), ("da", C.c_float), ("g0", C.c_float),
+                ("dg", C.c_float), ("drho", C.c_float)]
+
+
+class FitOpts(C.Structure):
+    _fields_ = [("K", C.c_int32), ("steps", C.c_int32), ("lr", C.c_float),
+                ("lambda_R", C.c_float), ("a_lo", C.c_float), ("a_hi", C.c_float),
+                ("g_lo", C.c_float), ("g_hi", C.c_float)]
+
+
+lib.sss_lut_fit.argtypes = [C.POINTER(Lut), C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
+                            C.c_void_p, C.POINTER(FitOpts), C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.c_void_p]
+lib.sss_lut_fit.restype = C.c_int
+
+
+def lut_fit(R_lut, p_lut, a0, da, g0, dg, drho, r_mm, P_mc, R_mc, raw, K=3, steps=1000,
+            lr=1e-2, lambda_R=5.0, a_rng=(0.0, 0.999), g_rng=(0.0, 0.95), want_grad=False,
+            stream=None):
+    """sss_lut_fit on CUDA float32 tensors; `raw` [n_prob][4K] is updated in
+    place.  Returns (loss [n_prob], grad [n_prob][4K] or None)."""
+    for t in (R_lut, p_lut, r_mm, P_mc, R_mc, raw):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    na, ng, nb = p_lut.shape
+    L = Lut(_ptr(R_lut), _ptr(p_lut), na, ng, nb, a0, da, g0, dg, drho)
+    o = FitOpts(K, steps, lr, lambda_R, a_rng[0], a_rng[1], g_rng[0], g_rng[1])
+    n = raw.shape[0]
+    loss = torch.empty(n, dtype=torch.float32, device=raw.device)
+    grad = torch.empty_like(raw) if want_grad else None
+    _check(lib.sss_lut_fit(C.byref(L), n, _ptr(r_mm), r_mm.numel(), _ptr(P_mc), _ptr(R_mc),
+                           C.byref(o), _ptr(raw), _ptr(loss), _ptr(grad), _stream(stream)),
+           "sss_lut_fit")
+    return loss, grad

@@ -58,6 +58,7 @@ bool opts_ok(const sss_walk_opts* o) {
   if (o->block_threads != 0 &&
       (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32)) return false;
   if (o->unit_paths < 0 || o->regroup < 0 || o->regroup > 32) return false;
+  if (o->incidence != 0 && o->incidence != 1) return false;
   return true;
 }
 
@@ -136,6 +137,8 @@ WalkConst make_const(const sss_params* p, const sss_walk_opts* o) {
   c.key1 = (uint32_t)(o->seed >> 32);
   c.path_offset = o->path_offset;
   c.inst_offset = o->instance_offset;
+  c.incidence = o->incidence;
+  c.entry_fresnel = o->entry_fresnel;
   for (int r = 0; r < 10; ++r) {
     c.rk[2 * r] = c.key0 + (uint32_t)r * 0x9E3779B9u;
     c.rk[2 * r + 1] = c.key1 + (uint32_t)r * 0xBB67AE85u;

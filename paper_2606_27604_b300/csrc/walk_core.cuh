@@ -85,6 +85,8 @@ struct WalkConst {
   uint32_t path_offset;
   uint32_t rk[20];   // Philox round keys derived from (key0, key1)
   uint32_t inst_offset;  // added to the instance index in the counters
+  int incidence;         // 0 normal, 1 cosine-weighted lobe
+  int entry_fresnel;
 };
 
 enum Event : int { EV_CONTINUE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_DEAD = 3, EV_TRUNC = 4 };
@@ -101,6 +103,36 @@ struct Path {
   float G;        // sum of d log p_HG / d g (adjoint)
   float gscale, glim, wsum;  // adjoint: fixed-point scale, per-path limit, sum(w)
 };
+
+// Hardware approximations (one MUFU operation each, a few ulp).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Unpolarised Fresnel reflectance, medium (index n) -> outside (index 1),
+// without branches: total internal reflection (n sin_i >= 1) and n = 1 are
+// selected at the end; the two quotients share one reciprocal.
+__device__ __forceinline__ float fresnel(float cos_i, float n) {
+  const float sin2_i = fmaxf(0.0f, __fmaf_rn(-cos_i, cos_i, 1.0f));
+  const float sin_t = __fmul_rn(n, sqrt_approx(sin2_i));
+  const float cos_t = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-sin_t, sin_t, 1.0f)));
+  const float nci = __fmul_rn(n, cos_i);
+  const float nct = __fmul_rn(n, cos_t);
+  const float sd = __fadd_rn(nci, cos_t), pd = __fadd_rn(cos_i, nct);
+  const float inv = rcp_approx(__fmul_rn(sd, pd));
+  const float rs = __fmul_rn(__fmul_rn(__fsub_rn(nci, cos_t), pd), inv);
+  const float rp = __fmul_rn(__fmul_rn(__fsub_rn(cos_i, nct), sd), inv);
+  float F = __fmul_rn(0.5f, __fmaf_rn(rs, rs, __fmul_rn(rp, rp)));
+  F = sin_t >= 1.0f ? 1.0f : F;
+  return n == 1.0f ? 0.0f : F;
+}
 
 // Medium choice: first k whose running binary32 CDF of w/sum(w) exceeds u.
 __device__ __forceinline__ int select_medium(const WalkConst& c, uint32_t inst, float u) {
@@ -137,6 +169,20 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.x = 0.0f; p.y = 0.0f; p.z = 0.0f;
   p.ux = 0.0f; p.uy = 0.0f; p.uz = 1.0f;
   p.W = c.W0;
+  if (c.incidence == 1) {
+    // cosine-weighted incident lobe: outside cosine sqrt(u), azimuth 2 pi u',
+    // refracted by Snell's law; entry weight 1 - F at the refracted angle
+    const uint4 e = philox4x32_10_rk(make_uint4(0u, path, inst + c.inst_offset, 2u), c.rk);
+    const float mu_o = sqrt_approx(u23(e.x));
+    const float sin_i = __fdividef(sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu_o, mu_o, 1.0f))),
+                                   c.n_rel);
+    float sp, cp;
+    __sincosf(__fmul_rn(6.2831853071795865f, __fsub_rn(u23(e.y), 0.5f)), &sp, &cp);
+    p.ux = -__fmul_rn(sin_i, cp);
+    p.uy = -__fmul_rn(sin_i, sp);
+    p.uz = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-sin_i, sin_i, 1.0f)));
+    p.W = c.entry_fresnel ? __fsub_rn(1.0f, fresnel(p.uz, c.n_rel)) : 1.0f;
+  }
   p.Aacc = 0.0f;
   p.step = 0u;
   p.path = path;
@@ -145,36 +191,6 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.n_coll = 0u;
   p.L = 0.0f;
   p.G = 0.0f;
-}
-
-// Hardware approximations (one MUFU operation each, a few ulp).
-__device__ __forceinline__ float sqrt_approx(float x) {
-  float y;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Unpolarised Fresnel reflectance, medium (index n) -> outside (index 1),
-// without branches: total internal reflection (n sin_i >= 1) and n = 1 are
-// selected at the end; the two quotients share one reciprocal.
-__device__ __forceinline__ float fresnel(float cos_i, float n) {
-  const float sin2_i = fmaxf(0.0f, __fmaf_rn(-cos_i, cos_i, 1.0f));
-  const float sin_t = __fmul_rn(n, sqrt_approx(sin2_i));
-  const float cos_t = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-sin_t, sin_t, 1.0f)));
-  const float nci = __fmul_rn(n, cos_i);
-  const float nct = __fmul_rn(n, cos_t);
-  const float sd = __fadd_rn(nci, cos_t), pd = __fadd_rn(cos_i, nct);
-  const float inv = rcp_approx(__fmul_rn(sd, pd));
-  const float rs = __fmul_rn(__fmul_rn(__fsub_rn(nci, cos_t), pd), inv);
-  const float rp = __fmul_rn(__fmul_rn(__fsub_rn(cos_i, nct), sd), inv);
-  float F = __fmul_rn(0.5f, __fmaf_rn(rs, rs, __fmul_rn(rp, rp)));
-  F = sin_t >= 1.0f ? 1.0f : F;
-  return n == 1.0f ? 0.0f : F;
 }
 
 // Henyey-Greenstein cosine by CDF inversion.  With xi = 2u - 1, the textbook

@@ -8,7 +8,8 @@ import oracle
 def to_oracle_opts(o):
     return oracle.OracleOpts(nbins=o.nbins, r_max_mm=o.r_max_mm, mode=o.mode,
                              rr_threshold=o.rr_threshold, entry_fresnel=o.entry_fresnel,
-                             max_steps=o.max_steps, seed=o.seed)
+                             max_steps=o.max_steps, seed=o.seed,
+                             incidence=getattr(o, "incidence", 0))
 
 
 def run_gpu(x, o, raw=False, media=None):

@@ -1,0 +1,160 @@
+"""The batched LUT fit (sss_lut_fit) against the FP64 reference, and an end
+to end fit of walk-generated mixture profiles with walk-built tables."""
+import numpy as np
+import pytest
+
+from oracle import lutfit as lf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_27604_b300 import api as a
+    return a
+
+
+def _tables(seed=0):
+    rng = np.random.default_rng(seed)
+    na, ng, nb = 12, 10, 48
+    a = np.linspace(0.0, 0.999, na)[:, None, None]
+    g = np.linspace(0.0, 0.95, ng)[None, :, None]
+    rho = (np.arange(nb) + 0.5)[None, None, :] * 0.25
+    lam = 0.4 + 2.0 * (1 - a) + 0.5 * g
+    p = (lam ** 2 / (2 * np.pi)) * np.exp(-lam * rho) * (1 + 0.05 * rng.uniform(size=(na, ng, nb)))
+    R = (0.9 * a ** 3 * (1 - 0.3 * g))[:, :, 0]
+    return R.astype(np.float32), p.astype(np.float32), 0.0, 0.999 / (na - 1), 0.0, 0.95 / (ng - 1), 0.25
+
+
+def test_loss_and_gradient_match_reference(api):
+    import torch
+    R, p, a0, da, g0, dg, drho = _tables()
+    tab = lf.Tables(R, p, a0, da, g0, dg, drho)
+    K, n = 3, 64
+    rng = np.random.default_rng(2)
+    raw = (rng.normal(size=(n, 4 * K)) * 0.6).astype(np.float32)
+    r = np.linspace(0.05, 3.0, 40).astype(np.float32)
+    P_mc = (0.3 * np.exp(-rng.uniform(0.5, 2.0, size=(n, 1)) * r[None, :]) + 1e-4).astype(np.float32)
+    P_mc[:, -3:] = 0.0          # empty bins are ignored
+    R_mc = rng.uniform(0.1, 0.6, size=n).astype(np.float32)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    raw_t = t(raw.copy())
+    loss, grad = api.lut_fit(t(R), t(p), a0, da, g0, dg, drho, t(r), t(P_mc), t(R_mc), raw_t,
+                             K=K, steps=0, want_grad=True)
+    loss, grad = loss.cpu().numpy(), grad.cpu().numpy()
+    for i in range(n):
+        L, gref = lf.loss_grad(raw[i].astype(np.float64), K, tab, r.astype(np.float64),
+                               P_mc[i].astype(np.float64), float(R_mc[i]))
+        assert loss[i] == pytest.approx(L, rel=2e-4, abs=1e-6)
+        np.testing.assert_allclose(grad[i], gref, rtol=2e-3, atol=2e-5 * np.abs(gref).max())
+
+
+def _model_problems(tab, K, n, seed, r):
+    rng = np.random.default_rng(seed)
+    truth = np.zeros((n, 4 * K))
+    truth[:, 0:K] = rng.uniform(0.0, 2.0, size=(n, K))
+    truth[:, K:2 * K] = rng.uniform(-1.0, 1.0, size=(n, K))
+    truth[:, 2 * K:3 * K] = np.log(rng.uniform(0.6, 1.8, size=(n, K)))
+    truth[:, 3 * K:] = rng.normal(size=(n, K)) * 0.5
+    P_mc = np.zeros((n, len(r))); R_mc = np.zeros(n)
+    for i in range(n):
+        a, g, s_, w, _, _ = lf.unpack(truth[i], K, (0.0, 0.999), (0.0, 0.95))
+        P_mc[i] = [sum(w[k] * s_[k] ** 2 * tab.p_at(a[k], g[k], s_[k] * ri)[0] for k in range(K))
+                   for ri in r]
+        R_mc[i] = sum(w[k] * tab.R_at(a[k], g[k])[0] for k in range(K))
+    return truth, P_mc, R_mc
+
+
+def test_adam_steps_match_reference(api):
+    # The first 20 Adam steps agree with the FP64 reference parameter for
+    # parameter (longer runs are compared by where they end: Adam turns tiny
+    # gradient components into full-size steps, so FP32 and FP64 runs may
+    # part on flat or symmetric stretches of the loss).
+    import torch
+    R, p, a0, da, g0, dg, drho = _tables(1)
+    tab = lf.Tables(R, p, a0, da, g0, dg, drho)
+    K, n, steps = 2, 8, 20
+    r = np.linspace(0.05, 3.0, 32)
+    truth, P_mc, R_mc = _model_problems(tab, K, n, 3, r)
+    start = truth + 0.1
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    raw_t = t(start)
+    loss, _ = api.lut_fit(t(R), t(p), a0, da, g0, dg, drho, t(r), t(P_mc), t(R_mc), raw_t,
+                          K=K, steps=steps, lr=1e-2)
+    got, loss = raw_t.cpu().numpy(), loss.cpu().numpy()
+    for i in range(n):
+        ref, Lref = lf.fit(np.float32(start[i]).astype(np.float64), K, tab, r, P_mc[i],
+                           R_mc[i], steps=steps, lr=1e-2)
+        np.testing.assert_allclose(got[i], ref, atol=2e-4)
+        assert loss[i] == pytest.approx(Lref, rel=1e-3, abs=1e-6)
+
+
+def test_adam_converges_on_model_generated_problems(api):
+    import torch
+    R, p, a0, da, g0, dg, drho = _tables(1)
+    tab = lf.Tables(R, p, a0, da, g0, dg, drho)
+    K, n = 2, 16
+    r = np.linspace(0.05, 3.0, 32)
+    truth, P_mc, R_mc = _model_problems(tab, K, n, 5, r)
+    start = truth + 0.1
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    loss0, _ = api.lut_fit(t(R), t(p), a0, da, g0, dg, drho, t(r), t(P_mc), t(R_mc), t(start),
+                           K=K, steps=0)
+    loss, _ = api.lut_fit(t(R), t(p), a0, da, g0, dg, drho, t(r), t(P_mc), t(R_mc), t(start),
+                          K=K, steps=600, lr=1e-2)
+    ratio = loss.cpu().numpy() / loss0.cpu().numpy()
+    print("final/start loss", np.round(ratio, 4))
+    assert np.median(ratio) < 1e-2 and np.mean(ratio < 0.1) >= 0.75
+
+
+def test_walk_lut_fit_chain_recovers_a_medium(api):
+    # walk -> tables (K = 1, sigma_t = 1) and walk -> target profile of one
+    # medium with sigma_t != 1; the fit through the tables brings the joint
+    # loss down tenfold, reproduces the reflectance and finds sigma_t (Eq. 5
+    # rescaling) to within the alpha-g-sigma_t trade-offs of a profile fit.
+    import torch
+    from paper_2606_27604_b300 import lut
+    alphas = np.linspace(0.5, 0.999, 24)
+    gs = np.linspace(0.0, 0.9, 12)
+    L = lut.build(alphas, gs, n_paths=1 << 17, nbins=64, r_max=16.0, n_rel=1.4, seed=5)
+    dens = L.density().astype(np.float32)
+    Rl = L.R.astype(np.float32)
+    n = 24
+    rng = np.random.default_rng(4)
+    a = rng.uniform(0.8, 0.98, size=(1, n)).astype(np.float32)
+    s = rng.uniform(1.0, 3.0, size=(1, n)).astype(np.float32)
+    g = rng.uniform(0.1, 0.8, size=(1, n)).astype(np.float32)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    m = api.Media(t(a), t(s), t(g), t(np.ones((1, n))), None, 1 << 17, None, 1.4)
+    nb, rmax = 32, 4.0
+    out = api.walk(m, api.WalkOptions(nbins=nb, r_max_mm=rmax, seed=77))
+    edges = np.linspace(0, rmax, nb + 1)
+    area = np.pi * (edges[1:] ** 2 - edges[:-1] ** 2)
+    Rm = out["R"].cpu().numpy()
+    P_mc = out["bins"].cpu().numpy() / Rm[:, None] / area[None, :]
+    P_mc = np.where(P_mc > 1e-2 * P_mc.max(axis=1, keepdims=True), P_mc, 0.0)
+    r = 0.5 * (edges[1:] + edges[:-1])
+    raw = np.zeros((n, 4))
+    raw_t = t(raw)
+    geo = (float(alphas[0]), float(alphas[1] - alphas[0]), float(gs[0]), float(gs[1] - gs[0]),
+           L.r_max / dens.shape[-1])
+    loss0, _ = api.lut_fit(t(Rl), t(dens), *geo, t(r), t(P_mc), t(Rm), t(raw), K=1, steps=0,
+                           a_rng=(0.5, 0.999), g_rng=(0.0, 0.9))
+    loss, _ = api.lut_fit(t(Rl), t(dens), *geo, t(r), t(P_mc), t(Rm), raw_t, K=1, steps=3000,
+                          lr=1e-2, a_rng=(0.5, 0.999), g_rng=(0.0, 0.9))
+    th = raw_t.cpu().numpy().astype(np.float64)
+    sig_fit = np.exp(th[:, 2])
+    print("loss median", float(loss0.median()), "->", float(loss.median()),
+          "sigma rel err median", np.median(np.abs(sig_fit / s[0] - 1)))
+    assert float(loss.median()) < 0.2 * float(loss0.median())
+    assert np.median(np.abs(sig_fit / s[0] - 1)) < 0.25
+    tab = lf.Tables(Rl, dens, *geo)
+    Rfit = []
+    for i in range(n):
+        a_, g_ = lf.unpack(th[i], 1, (0.5, 0.999), (0.0, 0.9))[:2]
+        Rfit.append(tab.R_at(float(a_[0]), float(g_[0]))[0])
+    Rfit = np.array(Rfit)
+    assert np.median(np.abs(Rfit / Rm - 1)) < 0.03

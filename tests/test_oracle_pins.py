@@ -219,6 +219,26 @@ def test_walk_matches_h_function_and_single_scatter():
                                    rtol=1e-12)
 
 
+def test_cosine_lobe_incidence_matches_h_function():
+    # cosine-weighted incident lobe: R = 2 int R(mu) mu dmu = 1 - 2 sqrt(1-a) int H mu dmu
+    for a in (0.5, 0.9, 0.99):
+        A, S, G, W = _single(a, K=1)
+        r = oracle.walk(A, S, G, W, np.array([1 << 17], np.uint32), None, 1.0,
+                        oracle.OracleOpts(incidence=1, seed=3))
+        Rc = hf.reflectance_cosine_lobe(a)
+        assert abs(r["R"][0] - Rc) <= Z * r["se_R"][0]
+        assert Rc > hf.reflectance_total(a)  # oblique light escapes more easily
+    # with a boundary the entry weight follows Fresnel at the refracted angle:
+    # alpha = 0 leaves only that specular loss, so A = 1 - <F>
+    A, S, G, W = _single(0.0, K=1)
+    r = oracle.walk(A, S, G, W, np.array([1 << 16], np.uint32), None, 1.4,
+                    oracle.OracleOpts(incidence=1, seed=4))
+    mu = (np.arange(20000) + 0.5) / 20000      # outside cosines, density 2 mu
+    ci = np.sqrt(1 - (1 - mu ** 2) / 1.4 ** 2)
+    Fm = np.mean([oracle.fresnel(c, 1.4) * 2 * m for c, m in zip(ci, mu)])
+    assert abs(r["A"][0] - (1 - Fm)) <= Z * r["se_A"][0] + 1e-4
+
+
 def test_zero_albedo_gives_no_reflectance():
     for n_rel in (1.0, 1.4):
         a, s, g, w = _single(0.0, 3.0, 0.5, n=2)

@@ -91,6 +91,26 @@ def test_independent_streams_agree_statistically(api):
     assert np.abs(zb).max() <= 5.0 and np.mean(np.abs(zb) <= 4.0) >= 0.995
 
 
+def test_cosine_lobe_incidence_parity(api):
+    # cosine-weighted entry (third Philox draw per path): same-stream parity
+    # with the oracle, and the closed form for the index-matched sets
+    x = inputs.single_wavelength(param_seed=0, n_paths=1 << 18)
+    o = opts(api, nbins=32, r_max_mm=10.0, seed=1000, incidence=1)
+    g, code, flags = run_gpu(x, o)
+    assert code == 0 and flags == 0
+    r = run_oracle(x, o)
+    worst, where = compare_same_stream(g, r, x.n_paths, r["steps"])
+    print("cosine-lobe same-stream worst ratio", worst, where)
+    assert worst <= 1.0, where
+    for i, a in enumerate(inputs.ALPHA_SET0):
+        assert abs(g["R"][i] - hf.reflectance_cosine_lobe(a)) <= 4 * g["stderr_R"][i]
+    x.n_rel = 1.4
+    g, _, _ = run_gpu(x, o)
+    r = run_oracle(x, o)
+    worst, where = compare_same_stream(g, r, x.n_paths, r["steps"])
+    assert worst <= 1.0, where
+
+
 def test_h_function_at_1e8_paths(api):
     # 2^27 paths per set: relative error <= 1e-3 and within 4 standard errors
     x = inputs.single_wavelength(param_seed=0, n_paths=1 << 27).subset(np.arange(10))
