@@ -43,6 +43,10 @@ class _Opts(C.Structure):
                 ("max_steps", C.c_uint32), ("seed", C.c_uint64), ("incidence", C.c_int)]
 
 
+class _Layer2(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("alpha2", "sigma_t2", "g2", "d1")]
+
+
 class _Out(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in
                 ("R", "T", "A", "bins", "overflow", "R_k", "R1", "truncated",
@@ -136,12 +140,21 @@ def _ids(inst_ids, n):
 
 
 def walk(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
-         opts: OracleOpts = OracleOpts(), path_offset: int = 0, inst_ids=None) -> dict:
+         opts: OracleOpts = OracleOpts(), path_offset: int = 0, inst_ids=None,
+         layer2=None) -> dict:
     """Mean tallies per instance (fractions of incident power) and their
     standard errors; see ``oracle_walk`` in ``walk_oracle.c``.  ``inst_ids``
     re-walks a subset of a larger batch under the instance numbers the
-    random-number counters had there."""
+    random-number counters had there.  ``layer2`` = (alpha2, sigma_t2, g2, d1),
+    float32 [n_inst] each, puts a second layer under the chosen medium:
+    the medium fills 0 <= z < d1, the second layer d1 <= z < thickness."""
     alpha, sigma_t, g, w, K, n = _check(alpha, sigma_t, g, w)
+    l2 = None
+    keep = None
+    if layer2 is not None:
+        keep = [_f32(a) for a in layer2]
+        assert all(k.shape == (n,) for k in keep)
+        l2 = _Layer2(*(_p(k) for k in keep))
     n_paths = np.ascontiguousarray(n_paths, dtype=np.uint32)
     assert n_paths.shape == (n,)
     th = None if thickness_mm is None else _f32(thickness_mm)
@@ -157,7 +170,8 @@ def walk(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
     o = opts._c()
     rc = _load().oracle_walk(C.c_int64(n), C.c_int(K), _p(alpha), _p(sigma_t), _p(g),
                              _p(w), _p(n_paths), _p(th), C.c_double(n_rel), C.byref(o),
-                             C.c_uint32(path_offset), _p(ids), C.byref(out))
+                             C.c_uint32(path_offset), _p(ids),
+                             C.byref(l2) if l2 is not None else None, C.byref(out))
     if rc != 0:
         raise ValueError("oracle_walk rejected its arguments")
     return res

@@ -182,6 +182,13 @@ typedef struct {
   int incidence;       /* 0 = normal, 1 = cosine-weighted lobe */
 } oracle_opts;
 
+/* Optional second layer under the chosen medium (two-layer slab, Sec. 3):
+ * the chosen medium fills 0 <= z < d1, this layer fills d1 <= z < thickness
+ * (semi-infinite when the thickness is +inf).  Arrays are [n_inst]. */
+typedef struct {
+  const float *alpha2, *sigma_t2, *g2, *d1;
+} oracle_layer2;
+
 typedef struct {
   int exit_kind;    /* 0 top, 1 bottom, 2 absorbed/roulette, 3 truncated */
   int medium;
@@ -198,10 +205,11 @@ typedef struct {
 /* inst indexes the parameter arrays; rng_inst is the instance number the
  * random-number counters use (the same unless a subset of a larger batch is
  * being re-walked). */
-void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
-                       const float* w, int K, int64_t n_inst, int64_t inst,
-                       uint32_t rng_inst, uint32_t path, double thickness_mm, double n_rel,
-                       const oracle_opts* o, oracle_path* res) {
+void oracle_trace_path_layered(const float* alpha, const float* sigma_t, const float* g,
+                               const float* w, int K, int64_t n_inst, int64_t inst,
+                               uint32_t rng_inst, uint32_t path, double thickness_mm,
+                               double n_rel, const oracle_opts* o, const oracle_layer2* l2,
+                               oracle_path* res) {
   double u[4];
   memset(res, 0, sizeof(*res));
   /* Medium selection once per path, before the walk (Eq. 4, Sec. 7). */
@@ -213,6 +221,15 @@ void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
   double a = alpha[(int64_t)k * n_inst + inst];
   double st = sigma_t[(int64_t)k * n_inst + inst];
   double gg = g[(int64_t)k * n_inst + inst];
+  /* optics of the other layer, swapped in when the path crosses z = d1 */
+  double a_o = 0.0, st_o = 1.0, g_o = 0.0, d1 = INFINITY;
+  if (l2) {
+    a_o = l2->alpha2[inst];
+    st_o = l2->sigma_t2[inst];
+    g_o = l2->g2[inst];
+    d1 = l2->d1[inst];
+  }
+  int layer = 0;
 
   /* Entry at the origin.  Normal incidence (Eq. 3), or a cosine-weighted
    * incident lobe (the fitting assumption of Sec. 8): outside cosine
@@ -241,16 +258,30 @@ void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
     draw4(o->seed, step, path, rng_inst, 0u, u);
     step++;
     double s = -log(u[0]) / st; /* exponential free flight (transmittance T) */
+    /* the planes bounding the current layer */
+    const double ztop = layer == 0 ? 0.0 : d1;
+    const double zbot = (l2 && layer == 0) ? d1 : d;
     double db = INFINITY;
-    if (dir[2] < 0.0) db = -pos[2] / dir[2];
-    else if (dir[2] > 0.0) db = (d - pos[2]) / dir[2];
+    if (dir[2] < 0.0) db = (ztop - pos[2]) / dir[2];
+    else if (dir[2] > 0.0) db = (zbot - pos[2]) / dir[2];
     if (db <= s) {
-      /* Reaches a face: move there, then smooth-dielectric Fresnel. */
       pos[0] += db * dir[0];
       pos[1] += db * dir[1];
       int top = dir[2] < 0.0;
-      pos[2] = top ? 0.0 : d;
       res->length += db;
+      if (l2 && ((top && layer == 1) || (!top && layer == 0))) {
+        /* Internal interface (index matched): cross into the other layer
+         * and draw a fresh flight there (flights are memoryless). */
+        pos[2] = d1;
+        layer ^= 1;
+        double t;
+        t = a; a = a_o; a_o = t;
+        t = st; st = st_o; st_o = t;
+        t = gg; gg = g_o; g_o = t;
+        continue;
+      }
+      /* Reaches an outer face: move there, then smooth-dielectric Fresnel. */
+      pos[2] = top ? 0.0 : d;
       double F = oracle_fresnel(fabs(dir[2]), n_rel);
       if (u[1] < F) { dir[2] = -dir[2]; continue; }
       res->exit_kind = top ? 0 : 1;
@@ -285,6 +316,14 @@ void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
   res->steps = step;
 }
 
+void oracle_trace_path(const float* alpha, const float* sigma_t, const float* g,
+                       const float* w, int K, int64_t n_inst, int64_t inst,
+                       uint32_t rng_inst, uint32_t path, double thickness_mm, double n_rel,
+                       const oracle_opts* o, oracle_path* res) {
+  oracle_trace_path_layered(alpha, sigma_t, g, w, K, n_inst, inst, rng_inst, path,
+                            thickness_mm, n_rel, o, NULL, res);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Batched forward tallies.                                                   */
 /* ------------------------------------------------------------------------ */
@@ -313,7 +352,8 @@ static double se_of(double s, double s2, double n) {
 int oracle_walk(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
                 const float* g, const float* w, const uint32_t* n_paths,
                 const float* thickness_mm, double n_rel, const oracle_opts* o,
-                uint32_t path_offset, const int64_t* inst_ids, oracle_out* out) {
+                uint32_t path_offset, const int64_t* inst_ids, const oracle_layer2* l2,
+                oracle_out* out) {
   if (K < 1 || K > ORC_KMAX || o->nbins < 1 || o->nbins > ORC_NBINS_MAX) return 1;
   const int nb = o->nbins;
   /* per-path vector: [bins nb][overflow][R_k K][R1][T][A][trunc][steps] */
@@ -333,9 +373,9 @@ int oracle_walk(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
       const int64_t p1 = (ch + 1) * ORC_CHUNK < (int64_t)N ? (ch + 1) * ORC_CHUNK : (int64_t)N;
       for (int64_t p = ch * ORC_CHUNK; p < p1; ++p) {
         oracle_path r;
-        oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i,
-                          inst_ids ? (uint32_t)inst_ids[i] : (uint32_t)i,
-                          path_offset + (uint32_t)p, d, n_rel, o, &r);
+        oracle_trace_path_layered(alpha, sigma_t, g, w, K, n_inst, i,
+                                  inst_ids ? (uint32_t)inst_ids[i] : (uint32_t)i,
+                                  path_offset + (uint32_t)p, d, n_rel, o, l2, &r);
         memset(c, 0, sizeof(double) * (size_t)nv);
         if (r.exit_kind == 0) {
           c[r.bin] = r.weight; /* bin or overflow slot */

@@ -344,6 +344,48 @@ def test_separability_of_extinction():
 
 
 # --------------------------------------------------------------------------
+# Two-layer slab (skin model of Sec. 3: a top slab over a second layer)
+# --------------------------------------------------------------------------
+def _layer2(a, s, g, d1, n=1):
+    f = lambda v: np.full(n, v, np.float32)
+    return (f(a), f(s), f(g), f(d1))
+
+
+def test_two_layer_limits_and_ballistic_transmittance():
+    N = np.array([100000], np.uint32)
+    o = oracle.OracleOpts(nbins=16, r_max_mm=4.0, seed=21)
+    A, S, G, W = _single(0.95, 2.0, 0.6, K=1)
+    one = oracle.walk(A, S, G, W, N, None, 1.4, o)
+    # identical layers behave like one layer (statistically: the crossing
+    # draws a fresh flight, which changes the random numbers, not the law)
+    two = oracle.walk(A, S, G, W, N, None, 1.4, o, layer2=_layer2(0.95, 2.0, 0.6, 0.3))
+    assert abs(two["R"][0] - one["R"][0]) <= Z * np.hypot(two["se_R"][0], one["se_R"][0])
+    # a vanishing top layer leaves the second layer alone
+    A2, S2, G2, _ = _single(0.8, 5.0, 0.2, K=1)
+    ref2 = oracle.walk(A2, S2, G2, W, N, None, 1.4, oracle.OracleOpts(nbins=16, r_max_mm=4.0, seed=5))
+    thin = oracle.walk(A, S, G, W, N, None, 1.4, o, layer2=_layer2(0.8, 5.0, 0.2, 1e-7))
+    assert abs(thin["R"][0] - ref2["R"][0]) <= Z * np.hypot(thin["se_R"][0], ref2["se_R"][0])
+    # a very thick top layer hides the second one
+    thick = oracle.walk(A, S, G, W, N, None, 1.4, o, layer2=_layer2(0.8, 5.0, 0.2, 1e4))
+    np.testing.assert_array_equal(thick["R"], one["R"])
+    # ballistic transmittance through both layers: alpha = 0, n = 1
+    A0, S1, G0, W1 = _single(0.0, 1.5, 0.0, K=1)
+    d1, D = 0.4, 1.1
+    r = oracle.walk(A0, S1, G0, W1, np.array([200000], np.uint32), np.array([D], np.float32),
+                    1.0, oracle.OracleOpts(nbins=8, mode=1, entry_fresnel=0, seed=9),
+                    layer2=_layer2(0.0, 3.0, 0.0, d1))
+    f = lambda v: float(np.float32(v))
+    Tc = math.exp(-f(1.5) * f(d1) - f(3.0) * (f(D) - f(d1)))
+    assert abs(r["T"][0] - Tc) <= Z * r["se_T"][0]
+    # analog path counts add up exactly with two layers
+    r = oracle.walk(_single(0.9, 2.0, 0.5, K=1)[0], S, G, W, np.array([20000], np.uint32),
+                    np.array([2.0], np.float32), 1.4,
+                    oracle.OracleOpts(nbins=8, mode=1, entry_fresnel=0, max_steps=2048),
+                    layer2=_layer2(0.7, 4.0, 0.3, 0.5))
+    assert (r["R"][0] + r["T"][0] + r["A"][0]) * 20000 + r["truncated"][0] == pytest.approx(20000, abs=1e-6)
+
+
+# --------------------------------------------------------------------------
 # Gradient estimator (score form of f_SSS, Sec. 4.1; mixture Eq. 4)
 # --------------------------------------------------------------------------
 def test_alpha_gradient_is_exact_derivative_of_crn_estimator():
