@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define SSS_ABI_VERSION 1
+#define SSS_ABI_VERSION 2
 #define SSS_KMAX 4          /* media per mixture supported (the paper uses 3) */
 #define SSS_NBINS_MAX 1024  /* radial bins supported */
 
@@ -76,7 +76,14 @@ typedef void* sss_stream_t; /* cudaStream_t */
  * thickness_mm: device float32 [n_inst] slab thickness (> 0; +inf for a
  *          semi-infinite slab), or NULL for all semi-infinite.
  * n_rel:   refractive index of the media relative to the outside (>= 1).
- * K in [1, SSS_KMAX]; n_inst in [0, 2^32). */
+ * K in [1, SSS_KMAX]; n_inst in [0, 2^32).
+ * alpha2, sigma_t2, g2, d1_mm: NULL, or device float32 [n_inst] each for a
+ *          two-layer slab (the skin model of Sec. 3): the chosen medium fills
+ *          the top layer 0 <= z < d1_mm, this second layer fills
+ *          d1_mm <= z < thickness (semi-infinite if thickness is +inf).  The
+ *          interface is index matched: a flight that reaches it stops there
+ *          and continues with a fresh flight in the other layer.  Forward
+ *          only (sss_walk_bwd returns SSS_ERR_UNSUPPORTED). */
 typedef struct {
   const float* alpha;
   const float* sigma_t;
@@ -88,6 +95,10 @@ typedef struct {
   float n_rel;
   int32_t K;
   int64_t n_inst;
+  const float* alpha2;
+  const float* sigma_t2;
+  const float* g2;
+  const float* d1_mm;
 } sss_params;
 
 /* Walk options (a zero-filled struct is NOT valid: call sss_walk_opts_default).
@@ -118,6 +129,12 @@ typedef struct {
  *                     number counters, so a shard [b, e) of a larger batch,
  *                     walked with instance_offset = b, reproduces that
  *                     batch's instances bit for bit (multi-GPU sharding).
+ *   log_r_min_mm    : 0 = linear bins (default).  > 0: logarithmic bins as
+ *                     in the paper's dataset generator (Sec. 3): bin 0 is
+ *                     [0, r_min), bin b >= 1 is [r_min q^(b-1), r_min q^b)
+ *                     with q = (r_max / r_min)^(1 / (nbins - 1)).
+ *                     Negative, non-finite, >= r_max_mm, or with nbins < 2:
+ *                     SSS_ERR_INVALID_ARG.
  *   incidence       : 0 = normal incidence at the origin (Eq. 3, default);
  *                     1 = cosine-weighted incident lobe (the fitting
  *                     illumination of Sec. 8): outside cosine sqrt(u),
@@ -141,6 +158,7 @@ typedef struct {
   int32_t regroup;
   uint32_t instance_offset;
   int32_t incidence;
+  float log_r_min_mm;
 } sss_walk_opts;
 
 /* Forward outputs, all float64 device arrays owned by the caller; any may be

@@ -180,6 +180,8 @@ typedef struct {
   uint32_t max_steps;
   uint64_t seed;
   int incidence;       /* 0 = normal, 1 = cosine-weighted lobe */
+  double log_r_min_mm; /* 0: linear bins; > 0: bin 0 = [0, r_min), then
+                          logarithmic edges r_min q^(b-1), q = (r_max/r_min)^(1/(nbins-1)) */
 } oracle_opts;
 
 /* Optional second layer under the chosen medium (two-layer slab, Sec. 3):
@@ -290,7 +292,15 @@ void oracle_trace_path_layered(const float* alpha, const float* sigma_t, const f
       res->y = pos[1];
       if (top) {
         double r = sqrt(pos[0] * pos[0] + pos[1] * pos[1]);
-        double fb = floor(r * (double)o->nbins / o->r_max_mm);
+        double fb;
+        if (o->log_r_min_mm > 0.0) {
+          fb = r < o->log_r_min_mm
+                   ? 0.0
+                   : 1.0 + floor(log(r / o->log_r_min_mm) /
+                                 (log(o->r_max_mm / o->log_r_min_mm) / (o->nbins - 1)));
+        } else {
+          fb = floor(r * (double)o->nbins / o->r_max_mm);
+        }
         res->bin = fb >= (double)o->nbins ? o->nbins : (int)fb;
       }
       break;

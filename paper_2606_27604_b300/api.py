@@ -33,7 +33,8 @@ class Params(C.Structure):
     _fields_ = [("alpha", C.c_void_p), ("sigma_t", C.c_void_p), ("g", C.c_void_p),
                 ("w", C.c_void_p), ("n_paths", C.c_void_p), ("uniform_paths", C.c_uint32),
                 ("thickness_mm", C.c_void_p), ("n_rel", C.c_float), ("K", C.c_int32),
-                ("n_inst", C.c_int64)]
+                ("n_inst", C.c_int64), ("alpha2", C.c_void_p), ("sigma_t2", C.c_void_p),
+                ("g2", C.c_void_p), ("d1_mm", C.c_void_p)]
 
 
 class Opts(C.Structure):
@@ -43,7 +44,7 @@ class Opts(C.Structure):
                 ("want_sumsq", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("block_threads", C.c_int32), ("unit_paths", C.c_int32),
                 ("regroup", C.c_int32), ("instance_offset", C.c_uint32),
-                ("incidence", C.c_int32)]
+                ("incidence", C.c_int32), ("log_r_min_mm", C.c_float)]
 
 
 class Tallies(C.Structure):
@@ -89,8 +90,13 @@ def _load():
     lib.sss_status_string.restype = C.c_char_p
     lib.sss_abi_version.argtypes = []
     lib.sss_abi_version.restype = C.c_int32
+    if lib.sss_abi_version() != ABI_VERSION:
+        raise ImportError(f"{LIB_PATH}: ABI version {lib.sss_abi_version()}, binding expects "
+                          f"{ABI_VERSION}; rebuild the library")
     return lib
 
+
+ABI_VERSION = 2  # struct layouts below match this version of the C header
 
 lib = _load()
 
@@ -132,6 +138,7 @@ class WalkOptions:
     regroup: int = 0
     instance_offset: int = 0
     incidence: int = 0
+    log_r_min_mm: float = 0.0
 
     def c(self) -> Opts:
         return Opts(**asdict(self))
@@ -148,6 +155,8 @@ class Media:
     uniform_paths: int = 0
     thickness_mm: Optional[torch.Tensor] = None
     n_rel: float = 1.0
+    # optional second layer of a two-layer slab: float32 [n] each
+    layer2: Optional[tuple] = None   # (alpha2, sigma_t2, g2, d1_mm)
 
     @property
     def K(self) -> int:
@@ -167,9 +176,13 @@ class Media:
             assert self.n_paths.numel() == self.n_inst
         if self.thickness_mm is not None:
             assert self.thickness_mm.is_cuda and self.thickness_mm.dtype == torch.float32
+        l2 = self.layer2 if self.layer2 is not None else (None,) * 4
+        for t in l2:
+            if t is not None:
+                assert t.is_cuda and t.dtype == torch.float32 and t.numel() == self.n_inst
         return Params(_ptr(self.alpha), _ptr(self.sigma_t), _ptr(self.g), _ptr(self.w),
                       _ptr(self.n_paths), self.uniform_paths, _ptr(self.thickness_mm),
-                      self.n_rel, self.K, self.n_inst)
+                      self.n_rel, self.K, self.n_inst, *(_ptr(t) for t in l2))
 
     @staticmethod
     def from_inputs(x, device="cuda", per_instance_paths: bool = None) -> "Media":
@@ -183,9 +196,11 @@ class Media:
             uniform = not per_instance_paths
         n_paths = None if uniform else torch.from_numpy(
             np.ascontiguousarray(x.n_paths, np.uint32).view(np.int32)).to(dev)
+        l2 = getattr(x, "layer2", None)
         return Media(f(x.alpha), f(x.sigma_t), f(x.g), f(x.w), n_paths,
                      int(x.n_paths[0]) if uniform else 0,
-                     None if x.thickness_mm is None else f(x.thickness_mm), float(x.n_rel))
+                     None if x.thickness_mm is None else f(x.thickness_mm), float(x.n_rel),
+                     None if l2 is None else tuple(f(a) for a in l2))
 
 
 def tally_count(nbins: int, K: int, want_sumsq: int) -> int:
@@ -303,7 +318,8 @@ class SSSWalk(torch.autograd.Function):
     def forward(ctx, alpha, sigma_t, g, w, template: Media, o: WalkOptions):
         m = Media(alpha.detach().contiguous(), sigma_t.detach().contiguous(),
                   g.detach().contiguous(), w.detach().contiguous(), template.n_paths,
-                  template.uniform_paths, template.thickness_mm, template.n_rel)
+                  template.uniform_paths, template.thickness_mm, template.n_rel,
+                  template.layer2)
         r = walk(m, o)
         ctx.m, ctx.o = m, o
         return r["R"], r["bins"], r["R_k"]

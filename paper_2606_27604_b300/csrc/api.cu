@@ -40,7 +40,10 @@ bool params_ok(const sss_params* p) {
   if (p->n_inst < 0 || p->n_inst > (int64_t)0xffffffffLL) return false;
   if (p->n_inst > 0 && (!p->alpha || !p->sigma_t || !p->g || !p->w)) return false;
   if (!(p->n_rel >= 1.0f) || !std::isfinite(p->n_rel)) return false;
-  const void* ptrs[] = {p->alpha, p->sigma_t, p->g, p->w, p->n_paths, p->thickness_mm};
+  const bool l2 = p->alpha2 || p->sigma_t2 || p->g2 || p->d1_mm;
+  if (l2 && !(p->alpha2 && p->sigma_t2 && p->g2 && p->d1_mm)) return false;  // all or none
+  const void* ptrs[] = {p->alpha, p->sigma_t, p->g, p->w, p->n_paths, p->thickness_mm,
+                        p->alpha2, p->sigma_t2, p->g2, p->d1_mm};
   for (const void* q : ptrs)
     if (q && (reinterpret_cast<uintptr_t>(q) & 3u)) return false;
   return true;
@@ -59,6 +62,8 @@ bool opts_ok(const sss_walk_opts* o) {
       (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32)) return false;
   if (o->unit_paths < 0 || o->regroup < 0 || o->regroup > 32) return false;
   if (o->incidence != 0 && o->incidence != 1) return false;
+  if (o->log_r_min_mm < 0.0f || !std::isfinite(o->log_r_min_mm)) return false;
+  if (o->log_r_min_mm > 0.0f && (o->log_r_min_mm >= o->r_max_mm || o->nbins < 2)) return false;
   return true;
 }
 
@@ -139,6 +144,16 @@ WalkConst make_const(const sss_params* p, const sss_walk_opts* o) {
   c.inst_offset = o->instance_offset;
   c.incidence = o->incidence;
   c.entry_fresnel = o->entry_fresnel;
+  c.log_bins = o->log_r_min_mm > 0.0f;
+  c.inv_rmin = c.log_bins ? (float)(1.0 / (double)o->log_r_min_mm) : 0.0f;
+  c.inv_log2q = c.log_bins && o->nbins > 1
+                    ? (float)((double)(o->nbins - 1) /
+                              std::log2((double)o->r_max_mm / (double)o->log_r_min_mm))
+                    : 0.0f;
+  c.alpha2 = p->alpha2;
+  c.sigma_t2 = p->sigma_t2;
+  c.g2 = p->g2;
+  c.d1 = p->d1_mm;
   for (int r = 0; r < 10; ++r) {
     c.rk[2 * r] = c.key0 + (uint32_t)r * 0x9E3779B9u;
     c.rk[2 * r + 1] = c.key1 + (uint32_t)r * 0xBB67AE85u;
@@ -195,7 +210,7 @@ sss_status persistent_shape(bool adj, const sss_params* p, const sss_walk_opts* 
   const int max_warps = (int)(kSmemLimit / per_warp);
   if (sh->block / 32 > max_warps) sh->block = max_warps * 32;
   sh->smem = (size_t)(sh->block / 32) * per_warp;
-  const void* fn = persistent_kernel_ptr(adj);
+  const void* fn = persistent_kernel_ptr(adj, p->alpha2 != nullptr);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit) !=
       cudaSuccess)
     return SSS_ERR_CUDA;
@@ -309,6 +324,7 @@ sss_status run(bool adj, const sss_params* p, const sss_walk_opts* o, void* ws, 
     return SSS_ERR_INVALID_ARG;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1))) return SSS_ERR_INVALID_ARG;
   if (adj && !gout) return SSS_ERR_INVALID_ARG;
+  if (adj && p->alpha2) return SSS_ERR_UNSUPPORTED;  // two-layer slabs: forward only
   const Layout L = make_layout(p, o, adj);
   if (wsb < L.total) return SSS_ERR_WORKSPACE;
   int sms = 0;

@@ -87,6 +87,11 @@ struct WalkConst {
   uint32_t inst_offset;  // added to the instance index in the counters
   int incidence;         // 0 normal, 1 cosine-weighted lobe
   int entry_fresnel;
+  // optional second layer (two-layer slab): [n_inst] each, or null
+  const float *alpha2, *sigma_t2, *g2, *d1;
+  // logarithmic radial bins: 1/r_min and 1/log2(q), or log_bins = 0
+  int log_bins;
+  float inv_rmin, inv_log2q;
 };
 
 enum Event : int { EV_CONTINUE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_DEAD = 3, EV_TRUNC = 4 };
@@ -101,6 +106,9 @@ struct Path {
   int k;
   float L;        // path length inside the medium (adjoint)
   float G;        // sum of d log p_HG / d g (adjoint)
+  // two-layer slab: optics of the other layer, interface depth, current layer
+  float a_o, fl_o, g_o, sigt_o, d1;
+  int layer;
   float gscale, glim, wsum;  // adjoint: fixed-point scale, per-path limit, sum(w)
 };
 
@@ -155,6 +163,7 @@ __device__ __forceinline__ int select_medium(const WalkConst& c, uint32_t inst, 
   return c.K - 1;
 }
 
+template <bool LAYERED = false>
 __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uint32_t path,
                                           float d, Path& p) {
   const uint4 r = philox4x32_10_rk(make_uint4(0u, path, inst + c.inst_offset, 1u), c.rk);
@@ -191,6 +200,14 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.n_coll = 0u;
   p.L = 0.0f;
   p.G = 0.0f;
+  if (LAYERED) {
+    p.layer = 0;
+    p.d1 = __ldg(c.d1 + inst);
+    p.a_o = __ldg(c.alpha2 + inst);
+    p.sigt_o = __ldg(c.sigma_t2 + inst);
+    p.fl_o = __fmul_rn(0.693147180559945309f, __fdiv_rn(1.0f, p.sigt_o));
+    p.g_o = __ldg(c.g2 + inst);
+  }
 }
 
 // Henyey-Greenstein cosine by CDF inversion.  With xi = 2u - 1, the textbook
@@ -222,7 +239,7 @@ __device__ __forceinline__ float hg_dlogp_dg(float g, float mu) {
 // collision (weighting, Henyey-Greenstein, rotation) arithmetic and selects
 // the outcome of the event it actually met, so lanes of a warp that meet
 // different events issue the same instructions.
-template <bool ADJ>
+template <bool ADJ, bool LAYERED = false>
 __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
   if (p.step >= c.max_steps) return EV_TRUNC;
   const uint4 r = philox4x32_10_rk(make_uint4(p.step, p.path, p.cinst, 0u), c.rk);
@@ -235,19 +252,29 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
   // Distance to the face the path is heading to.
   const float iuz = rcp_approx(p.uz);
   const float inf = __int_as_float(0x7f800000);
-  const float db = p.uz < 0.0f ? __fmul_rn(-p.z, iuz)
-                               : (p.uz > 0.0f ? __fmul_rn(__fsub_rn(p.d, p.z), iuz) : inf);
-  const bool hit = db <= s;
+  float db;
+  bool cross = false;  // reaches the internal interface of a two-layer slab
   const bool top = p.uz < 0.0f;
+  if (!LAYERED) {
+    db = p.uz < 0.0f ? __fmul_rn(-p.z, iuz)
+                     : (p.uz > 0.0f ? __fmul_rn(__fsub_rn(p.d, p.z), iuz) : inf);
+  } else {
+    const float ztop = p.layer ? p.d1 : 0.0f;
+    const float zbot = p.layer ? p.d : p.d1;
+    db = p.uz < 0.0f ? __fmul_rn(__fsub_rn(ztop, p.z), iuz)
+                     : (p.uz > 0.0f ? __fmul_rn(__fsub_rn(zbot, p.z), iuz) : inf);
+  }
+  const bool hit = db <= s;
+  if (LAYERED) cross = hit && (top == (p.layer == 1));
   const float dist = hit ? db : s;
   p.x = __fmaf_rn(dist, p.ux, p.x);
   p.y = __fmaf_rn(dist, p.uy, p.y);
-  p.z = hit ? (top ? 0.0f : p.d) : __fmaf_rn(dist, p.uz, p.z);
+  p.z = hit ? (cross ? p.d1 : (top ? 0.0f : p.d)) : __fmaf_rn(dist, p.uz, p.z);
   if (ADJ) p.L = __fadd_rn(p.L, dist);
 
   // Face: smooth-dielectric Fresnel, reflect with probability F.
   const float F = fresnel(fabsf(p.uz), c.n_rel);
-  const bool reflect = hit && (u1 < F);
+  const bool reflect = hit && !cross && (u1 < F);
 
   // Collision: albedo weighting with roulette, or analog absorption.
   bool dead;
@@ -293,15 +320,27 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
   p.uy = hit ? p.uy : __fmul_rn(ny, inr);
   p.uz = uz_new;
 
+  if (LAYERED && cross) {  // continue in the other layer with a fresh flight
+    float t;
+    t = p.alpha; p.alpha = p.a_o; p.a_o = t;
+    t = p.fl; p.fl = p.fl_o; p.fl_o = t;
+    t = p.g; p.g = p.g_o; p.g_o = t;
+    t = p.sigt; p.sigt = p.sigt_o; p.sigt_o = t;
+    p.layer ^= 1;
+    return EV_CONTINUE;
+  }
   if (dead) return EV_DEAD;
   if (hit && !reflect) return top ? EV_TOP : EV_BOTTOM;
   return EV_CONTINUE;
 }
 
-// Radial bin of a top exit (nbins = overflow).
+// Radial bin of a top exit (nbins = overflow), linear or logarithmic.
 __device__ __forceinline__ int exit_bin(const WalkConst& c, const Path& p) {
   const float rr = sqrt_approx(__fmaf_rn(p.x, p.x, __fmul_rn(p.y, p.y)));
-  return (int)fminf(floorf(__fmul_rn(rr, c.bin_scale)), (float)c.nbins);
+  if (!c.log_bins) return (int)fminf(floorf(__fmul_rn(rr, c.bin_scale)), (float)c.nbins);
+  const float t = __fmul_rn(rr, c.inv_rmin);
+  if (t < 1.0f) return 0;
+  return (int)fminf(1.0f + floorf(__fmul_rn(__log2f(t), c.inv_log2q)), (float)c.nbins);
 }
 
 }  // namespace sss

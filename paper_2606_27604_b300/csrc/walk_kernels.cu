@@ -48,9 +48,14 @@ __global__ void validate_params_kernel(WalkConst c, unsigned int* status) {
     wsum += w;
   }
   bad |= !(fabsf(wsum - 1.0f) <= 1e-5f);
-  if (c.thickness) {
-    const float d = c.thickness[i];
-    bad |= !(d > 0.0f);  // +inf allowed, NaN and <= 0 rejected
+  const float d = c.thickness ? c.thickness[i] : __int_as_float(0x7f800000);
+  if (c.thickness) bad |= !(d > 0.0f);  // +inf allowed, NaN and <= 0 rejected
+  if (c.alpha2) {
+    const float a = c.alpha2[i], s = c.sigma_t2[i], g = c.g2[i], d1 = c.d1[i];
+    bad |= !(a >= 0.0f && a <= 1.0f);
+    bad |= !(s > 0.0f && s < __int_as_float(0x7f800000));
+    bad |= !(g > -1.0f && g < 1.0f);
+    bad |= !(d1 > 0.0f && d1 <= d);
   }
   if (bad) atomicOr(status, SSS_DEV_FLAG_PARAM);
 }
@@ -256,7 +261,7 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
   if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
 }
 
-template <bool ADJ>
+template <bool ADJ, bool LAYERED>
 __global__ void __launch_bounds__(256)
 walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   extern __shared__ unsigned long long smem[];
@@ -352,7 +357,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
           const int rank = __popc(idle & ((1u << lane) - 1u));
           __syncwarp();
           if (st == LANE_IDLE && (uint32_t)rank < take) {
-            path_init(c, meta[cur].inst, c.path_offset + nxt + rank, meta[cur].d, p);
+            path_init<LAYERED>(c, meta[cur].inst, c.path_offset + nxt + rank, meta[cur].d, p);
             if (ADJ) {
               p.gscale = meta[cur].scale;
               p.glim = meta[cur].lim;
@@ -386,7 +391,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     }
     // ---- advance every running path by one draw ----
     if (st == LANE_RUNNING) {
-      ev = path_step<ADJ>(c, p);
+      ev = path_step<ADJ, LAYERED>(c, p);
       if (ev != EV_CONTINUE) st = LANE_DONE;
     }
   }
@@ -397,6 +402,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
 
 // ------------------------------------------------------------------ plain --
 // One thread per path of a single instance; block-level shared tallies.
+template <bool LAYERED>
 __global__ void __launch_bounds__(256)
 walk_plain_kernel(WalkConst c, WalkSched s, TallyOut t, uint32_t inst, uint32_t N) {
   extern __shared__ unsigned long long smem[];
@@ -407,10 +413,10 @@ walk_plain_kernel(WalkConst c, WalkSched s, TallyOut t, uint32_t inst, uint32_t 
   if (j < N) {
     Path p;
     const float d = c.thickness ? c.thickness[inst] : __int_as_float(0x7f800000);
-    path_init(c, inst, c.path_offset + j, d, p);
+    path_init<LAYERED>(c, inst, c.path_offset + j, d, p);
     int ev;
     do {
-      ev = path_step<false>(c, p);
+      ev = path_step<false, LAYERED>(c, p);
     } while (ev == EV_CONTINUE);
     const int nb = c.nbins;
     if (ev == EV_TOP) {
@@ -536,19 +542,24 @@ void launch_unit_prefix(const uint32_t* n_paths, uint32_t n, uint32_t C,
 void launch_walk_persistent(bool adj, int grid, int block, size_t smem, const WalkConst& c,
                             const WalkSched& s, const TallyOut& t, const GradIn& gi,
                             cudaStream_t st) {
-  if (adj) walk_persistent_kernel<true><<<grid, block, smem, st>>>(c, s, t, gi);
-  else walk_persistent_kernel<false><<<grid, block, smem, st>>>(c, s, t, gi);
+  if (adj) walk_persistent_kernel<true, false><<<grid, block, smem, st>>>(c, s, t, gi);
+  else if (c.alpha2) walk_persistent_kernel<false, true><<<grid, block, smem, st>>>(c, s, t, gi);
+  else walk_persistent_kernel<false, false><<<grid, block, smem, st>>>(c, s, t, gi);
 }
 
-const void* persistent_kernel_ptr(bool adj) {
-  return adj ? (const void*)walk_persistent_kernel<true>
-             : (const void*)walk_persistent_kernel<false>;
+const void* persistent_kernel_ptr(bool adj, bool layered) {
+  return adj ? (const void*)walk_persistent_kernel<true, false>
+             : (layered ? (const void*)walk_persistent_kernel<false, true>
+                        : (const void*)walk_persistent_kernel<false, false>);
 }
 
 void launch_walk_plain(const WalkConst& c, const WalkSched& s, const TallyOut& t, uint32_t inst,
                        uint32_t N, cudaStream_t st) {
   if (N == 0) return;
-  walk_plain_kernel<<<(N + 255) / 256, 256, (size_t)s.slot_words * 8, st>>>(c, s, t, inst, N);
+  if (c.alpha2)
+    walk_plain_kernel<true><<<(N + 255) / 256, 256, (size_t)s.slot_words * 8, st>>>(c, s, t, inst, N);
+  else
+    walk_plain_kernel<false><<<(N + 255) / 256, 256, (size_t)s.slot_words * 8, st>>>(c, s, t, inst, N);
 }
 
 void launch_finalize_tallies(const WalkConst& c, const WalkSched& s, const TallyOut& t,

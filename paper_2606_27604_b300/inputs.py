@@ -51,6 +51,8 @@ class WalkInputs:
     n_rel: float = 1.0
     lambda_nm: Optional[np.ndarray] = None     # float32 [n], label only
     meta: dict = field(default_factory=dict)
+    # optional second layer of a two-layer slab: (alpha2, sigma_t2, g2, d1_mm)
+    layer2: Optional[tuple] = None
 
     @property
     def n_inst(self) -> int:
@@ -72,7 +74,9 @@ class WalkInputs:
             else np.ascontiguousarray(self.thickness_mm[idx]),
             n_rel=self.n_rel,
             lambda_nm=None if self.lambda_nm is None else self.lambda_nm[idx],
-            meta=dict(self.meta, subset=True))
+            meta=dict(self.meta, subset=True),
+            layer2=None if self.layer2 is None
+            else tuple(np.ascontiguousarray(a[idx]) for a in self.layer2))
 
 
 def _dirichlet_ones(rng, shape_lead, K):
@@ -193,6 +197,28 @@ def decoder_weights(seed: int = 4) -> dict:
             bb = torch.from_numpy(b.astype(np.float32)).to(torch.bfloat16).float().numpy()
             out[f"{net}{l}"] = (Wb, bb)
     return out
+
+
+def two_layer_batch(n_inst: int = 1024, param_seed: int = 6, n_paths: int = 1 << 14,
+                    n_rel: float = 1.4) -> WalkInputs:
+    """Two-layer slabs shaped like the paper's skin model (Sec. 3): a thin,
+    absorbing, forward-scattering top layer of 50-350 um over a
+    semi-infinite, high-albedo second layer.  Synthetic optics (the
+    chromophore spectra are not available): top alpha ~ U[0.3, 0.95],
+    log10 sigma_t ~ U[1, 2] mm^-1, g ~ U[0.7, 0.9]; second alpha ~
+    U[0.9, 0.999], log10 sigma_t ~ U[0.5, 1.5], g ~ U[0.6, 0.9]; one medium
+    per path (K = 1)."""
+    rng = np.random.default_rng(param_seed)
+    f = lambda lo, hi: rng.uniform(lo, hi, size=n_inst).astype(np.float32)
+    a1, s1, g1 = f(0.3, 0.95), (10 ** f(1.0, 2.0)).astype(np.float32), f(0.7, 0.9)
+    a2, s2, g2 = f(0.9, 0.999), (10 ** f(0.5, 1.5)).astype(np.float32), f(0.6, 0.9)
+    d1 = f(0.05, 0.35)
+    one = np.ones((1, n_inst), np.float32)
+    return WalkInputs(a1[None].copy(), s1[None].copy(), g1[None].copy(), one,
+                      np.full(n_inst, n_paths, dtype=np.uint32), None, n_rel,
+                      np.full(n_inst, 550.0, np.float32),
+                      meta=dict(name="two_layer_batch", param_seed=param_seed),
+                      layer2=(a2, s2, g2, d1))
 
 
 def rgb_texture(side: int = 1024, seed: int = 4) -> np.ndarray:

@@ -9,7 +9,8 @@ def to_oracle_opts(o):
     return oracle.OracleOpts(nbins=o.nbins, r_max_mm=o.r_max_mm, mode=o.mode,
                              rr_threshold=o.rr_threshold, entry_fresnel=o.entry_fresnel,
                              max_steps=o.max_steps, seed=o.seed,
-                             incidence=getattr(o, "incidence", 0))
+                             incidence=getattr(o, "incidence", 0),
+                             log_r_min_mm=getattr(o, "log_r_min_mm", 0.0))
 
 
 def run_gpu(x, o, raw=False, media=None):
@@ -25,7 +26,8 @@ def run_gpu(x, o, raw=False, media=None):
 
 def run_oracle(x, o, inst_ids=None, path_offset=0):
     return oracle.walk(x.alpha, x.sigma_t, x.g, x.w, x.n_paths, x.thickness_mm, x.n_rel,
-                       to_oracle_opts(o), path_offset=path_offset, inst_ids=inst_ids)
+                       to_oracle_opts(o), path_offset=path_offset, inst_ids=inst_ids,
+                       layer2=getattr(x, "layer2", None))
 
 
 TALLIES = ("R", "T", "A", "bins", "overflow", "R_k", "R1")

@@ -351,6 +351,20 @@ def _layer2(a, s, g, d1, n=1):
     return (f(a), f(s), f(g), f(d1))
 
 
+def test_log_bins_partition_the_same_exits():
+    # logarithmic bins (512 to 50 mm, as the paper's generator) regroup the
+    # same exits: their sum equals the linear bins' sum plus overflow, and a
+    # bin's content equals the linear tally over the same radii
+    A, S, G, W = _single(0.97, 2.0, 0.8, K=1)
+    N = np.array([50000], np.uint32)
+    lin = oracle.walk(A, S, G, W, N, None, 1.4, oracle.OracleOpts(nbins=50, r_max_mm=50.0, seed=8))
+    lg = oracle.walk(A, S, G, W, N, None, 1.4,
+                     oracle.OracleOpts(nbins=512, r_max_mm=50.0, seed=8, log_r_min_mm=1.0))
+    np.testing.assert_allclose(lg["bins"].sum() + lg["overflow"][0], lin["R"][0], rtol=1e-12)
+    np.testing.assert_allclose(lg["bins"][0, 0], lin["bins"][0, 0], rtol=1e-12)  # [0, 1 mm)
+    np.testing.assert_allclose(lg["overflow"], lin["overflow"], rtol=1e-12)
+
+
 def test_two_layer_limits_and_ballistic_transmittance():
     N = np.array([100000], np.uint32)
     o = oracle.OracleOpts(nbins=16, r_max_mm=4.0, seed=21)

@@ -111,6 +111,49 @@ def test_cosine_lobe_incidence_parity(api):
     assert worst <= 1.0, where
 
 
+def test_log_radial_bins_parity(api):
+    # 512 logarithmic bins to 50 mm as in the dataset generator of Sec. 3,
+    # innermost edge 10 um: same-stream parity, and the bins plus overflow
+    # hold exactly the top-exit weight that the linear bins hold
+    x = inputs.spectral_field(n_texels=3, param_seed=4, n_paths=6000)
+    o = opts(api, nbins=512, r_max_mm=50.0, seed=77, log_r_min_mm=0.01)
+    g, code, flags = run_gpu(x, o, raw=True)
+    assert code == 0 and flags == 0
+    r = run_oracle(x, o)
+    worst, where = compare_same_stream(g, r, x.n_paths, r["steps"])
+    print("log-bin same-stream worst ratio", worst, where)
+    assert worst <= 1.0, where
+    gl, _, _ = run_gpu(x, opts(api, nbins=64, r_max_mm=50.0, seed=77), raw=True)
+    nb = 512
+    exits_log = g["raw"][:, :nb + 1].sum(axis=1)
+    exits_lin = gl["raw"][:, :65].sum(axis=1)
+    np.testing.assert_array_equal(exits_log, exits_lin)
+
+
+def test_two_layer_slab_parity_and_limits(api):
+    # skin-like two-layer slabs: same-stream parity with the oracle, the
+    # plain baseline bit-identical, and a top layer too thick to cross
+    # reproducing the one-layer walk bit for bit
+    x = inputs.two_layer_batch(n_inst=128, param_seed=6, n_paths=1 << 14)
+    o = opts(api, nbins=64, r_max_mm=10.0, seed=2026)
+    g, code, flags = run_gpu(x, o, raw=True)
+    assert code == 0 and flags == 0
+    r = run_oracle(x, o)
+    worst, where = compare_same_stream(g, r, x.n_paths, r["steps"])
+    print("two-layer same-stream worst ratio", worst, where)
+    assert worst <= 1.0, where
+    gp, _, _ = run_gpu(x, opts(api, nbins=64, r_max_mm=10.0, seed=2026, schedule=1), raw=True)
+    np.testing.assert_array_equal(g["raw"], gp["raw"])
+    thick = x.subset(np.arange(x.n_inst))
+    thick.layer2 = thick.layer2[:3] + (np.full(x.n_inst, 1e4, np.float32),)
+    gt, _, _ = run_gpu(thick, o, raw=True)
+    one = x.subset(np.arange(x.n_inst)); one.layer2 = None
+    g1, _, _ = run_gpu(one, o, raw=True)
+    np.testing.assert_array_equal(gt["raw"], g1["raw"])
+    # the second layer matters: reflectance differs from the top layer alone
+    assert np.mean(np.abs(g["R"] - g1["R"])) > 10 * np.mean(g["stderr_R"])
+
+
 def test_h_function_at_1e8_paths(api):
     # 2^27 paths per set: relative error <= 1e-3 and within 4 standard errors
     x = inputs.single_wavelength(param_seed=0, n_paths=1 << 27).subset(np.arange(10))
