@@ -140,7 +140,14 @@ typedef struct {
  *                     illumination of Sec. 8): outside cosine sqrt(u),
  *                     azimuth 2 pi u' from a third Philox draw per path
  *                     (tag 2), refracted by Snell's law, entry weight 1 - F
- *                     at the refracted angle when entry_fresnel = 1. */
+ *                     at the refracted angle when entry_fresnel = 1.
+ *   select_pdf      : how a path picks its medium, once, before the walk.
+ *                     0 = with probability w_k / sum(w) (Sec. 7, default);
+ *                     1 = uniformly among the K media, the path weight
+ *                     multiplied by K w_k / sum(w) so the mixture of Eq. 4
+ *                     is estimated without bias (Sec. 7 leaves other
+ *                     choices open).  Other values: SSS_ERR_INVALID_ARG.
+ */
 typedef struct {
   int32_t nbins;
   float r_max_mm;
@@ -159,6 +166,7 @@ typedef struct {
   uint32_t instance_offset;
   int32_t incidence;
   float log_r_min_mm;
+  int32_t select_pdf;
 } sss_walk_opts;
 
 /* Forward outputs, all float64 device arrays owned by the caller; any may be

@@ -41,7 +41,7 @@ class _Opts(C.Structure):
     _fields_ = [("nbins", C.c_int), ("r_max_mm", C.c_double), ("mode", C.c_int),
                 ("rr_threshold", C.c_double), ("entry_fresnel", C.c_int),
                 ("max_steps", C.c_uint32), ("seed", C.c_uint64), ("incidence", C.c_int),
-                ("log_r_min_mm", C.c_double)]
+                ("log_r_min_mm", C.c_double), ("select_pdf", C.c_int)]
 
 
 class _Layer2(C.Structure):
@@ -74,11 +74,12 @@ class OracleOpts:
     seed: int = 1000
     incidence: int = 0
     log_r_min_mm: float = 0.0
+    select_pdf: int = 0
 
     def _c(self):
         return _Opts(self.nbins, self.r_max_mm, self.mode, self.rr_threshold,
                      self.entry_fresnel, self.max_steps, self.seed, self.incidence,
-                     self.log_r_min_mm)
+                     self.log_r_min_mm, self.select_pdf)
 
 
 def _p(a):

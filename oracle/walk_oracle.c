@@ -182,6 +182,8 @@ typedef struct {
   int incidence;       /* 0 = normal, 1 = cosine-weighted lobe */
   double log_r_min_mm; /* 0: linear bins; > 0: bin 0 = [0, r_min), then
                           logarithmic edges r_min q^(b-1), q = (r_max/r_min)^(1/(nbins-1)) */
+  int select_pdf;      /* 0: medium k with probability w_k / sum(w) (Sec. 7);
+                          1: uniformly, with path weight K w_k / sum(w) */
 } oracle_opts;
 
 /* Optional second layer under the chosen medium (two-layer slab, Sec. 3):
@@ -218,7 +220,20 @@ void oracle_trace_path_layered(const float* alpha, const float* sigma_t, const f
   float wk[ORC_KMAX];
   for (int k = 0; k < K; ++k) wk[k] = w[(int64_t)k * n_inst + inst];
   draw4(o->seed, 0u, path, rng_inst, 1u, u);
-  int k = oracle_select_medium(wk, K, u[0]);
+  int k;
+  double w_sel = 1.0; /* w_k / (p_k sum(w)): the estimator weight of the choice */
+  if (o->select_pdf == 1) {
+    /* another selection pdf (Sec. 7 samples by w_k and leaves others
+     * open): uniform over the K media, reweighted so that the mixture
+     * of Eq. 4 is still estimated without bias */
+    k = (int)floor(u[0] * (double)K);
+    if (k > K - 1) k = K - 1;
+    double tot = 0.0;
+    for (int j = 0; j < K; ++j) tot += (double)wk[j];
+    w_sel = (double)K * (double)wk[k] / tot;
+  } else {
+    k = oracle_select_medium(wk, K, u[0]);
+  }
   res->medium = k;
   double a = alpha[(int64_t)k * n_inst + inst];
   double st = sigma_t[(int64_t)k * n_inst + inst];
@@ -251,7 +266,7 @@ void oracle_trace_path_layered(const float* alpha, const float* sigma_t, const f
     dir[1] = sin_i * sin(phi);
     dir[2] = sqrt(1.0 - sin_i * sin_i);
   }
-  double W = o->entry_fresnel ? 1.0 - oracle_fresnel(dir[2], n_rel) : 1.0;
+  double W = (o->entry_fresnel ? 1.0 - oracle_fresnel(dir[2], n_rel) : 1.0) * w_sel;
   double d = thickness_mm; /* +inf: semi-infinite */
 
   uint32_t step = 0;
@@ -496,7 +511,7 @@ int oracle_walk_grad(int64_t n_inst, int K, const float* alpha, const float* sig
           if (grad_T) v += grad_T[i];
         }
         double c[4 * ORC_KMAX] = {0};
-        if (v != 0.0) {
+        if (v != 0.0 && r.weight != 0.0) {
           const int k = r.medium;
           const double a = alpha[(int64_t)k * n_inst + i];
           const double st = sigma_t[(int64_t)k * n_inst + i];

@@ -44,7 +44,8 @@ class Opts(C.Structure):
                 ("want_sumsq", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("block_threads", C.c_int32), ("unit_paths", C.c_int32),
                 ("regroup", C.c_int32), ("instance_offset", C.c_uint32),
-                ("incidence", C.c_int32), ("log_r_min_mm", C.c_float)]
+                ("incidence", C.c_int32), ("log_r_min_mm", C.c_float),
+                ("select_pdf", C.c_int32)]
 
 
 class Tallies(C.Structure):
@@ -139,6 +140,7 @@ class WalkOptions:
     instance_offset: int = 0
     incidence: int = 0
     log_r_min_mm: float = 0.0
+    select_pdf: int = 0
 
     def c(self) -> Opts:
         return Opts(**asdict(self))

@@ -62,6 +62,7 @@ bool opts_ok(const sss_walk_opts* o) {
       (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32)) return false;
   if (o->unit_paths < 0 || o->regroup < 0 || o->regroup > 32) return false;
   if (o->incidence != 0 && o->incidence != 1) return false;
+  if (o->select_pdf != 0 && o->select_pdf != 1) return false;
   if (o->log_r_min_mm < 0.0f || !std::isfinite(o->log_r_min_mm)) return false;
   if (o->log_r_min_mm > 0.0f && (o->log_r_min_mm >= o->r_max_mm || o->nbins < 2)) return false;
   return true;
@@ -144,6 +145,7 @@ WalkConst make_const(const sss_params* p, const sss_walk_opts* o) {
   c.inst_offset = o->instance_offset;
   c.incidence = o->incidence;
   c.entry_fresnel = o->entry_fresnel;
+  c.select_uniform = o->select_pdf == 1;
   c.log_bins = o->log_r_min_mm > 0.0f;
   c.inv_rmin = c.log_bins ? (float)(1.0 / (double)o->log_r_min_mm) : 0.0f;
   c.inv_log2q = c.log_bins && o->nbins > 1
@@ -192,7 +194,7 @@ std::string graph_key(int tag, const sss_params* p, const sss_walk_opts* o, cons
 
 // Launch configuration of the persistent kernel.
 struct Shape {
-  int block, grid, regroup, burst;
+  int block, grid, regroup;
   uint32_t unit_paths;
   size_t smem;
 };
@@ -201,11 +203,10 @@ sss_status persistent_shape(bool adj, const sss_params* p, const sss_walk_opts* 
                             int sms, Shape* sh) {
   constexpr size_t kSmemLimit = 200 * 1024;
   sh->block = o->block_threads ? o->block_threads : 256;
-  sh->regroup = o->regroup ? o->regroup : 6;
-  sh->burst = 1;
-  sh->unit_paths = o->unit_paths ? (uint32_t)o->unit_paths : 2048u;
+  sh->regroup = o->regroup ? o->regroup : 8;
+  sh->unit_paths = o->unit_paths ? (uint32_t)o->unit_paths : 1024u;
   // two slots of accumulators per warp; shrink the block for wide histograms
-  const size_t per_warp = (size_t)2 * acc_words * 8 + 2 * 32;  // + two 32-byte slot headers
+  const size_t per_warp = (size_t)2 * acc_words * 8 + 2 * kSlotMetaBytes;  // + slot headers
   if (per_warp > kSmemLimit) return SSS_ERR_INVALID_ARG;
   const int max_warps = (int)(kSmemLimit / per_warp);
   if (sh->block / 32 > max_warps) sh->block = max_warps * 32;
@@ -249,7 +250,6 @@ sss_status enqueue_walk(bool adj, const sss_params* p, const sss_walk_opts* o, v
   s.unit_counter = counter;
   s.unit_paths = sh.unit_paths ? sh.unit_paths : 1024u;
   s.regroup = sh.regroup;
-  s.burst = sh.burst ? sh.burst : 1;
   s.slot_words = L.acc_words;
   s.want_sumsq = o->want_sumsq;
   s.status = status;

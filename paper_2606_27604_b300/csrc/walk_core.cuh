@@ -43,14 +43,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // The same block with the key schedule precomputed: rk[2r], rk[2r+1] are the
 // round-r keys (k0 + r W0, k1 + r W1).  With rk in the kernel's parameter
 // (constant) bank the XORs read it directly, so the key additions vanish.
+// Each round's two products are taken as one 32x32->64 multiply each.
 __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53ull;
+    const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57ull;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * r + 1], (uint32_t)p0);
   }
   return c;
 }
@@ -92,6 +92,7 @@ struct WalkConst {
   // logarithmic radial bins: 1/r_min and 1/log2(q), or log_bins = 0
   int log_bins;
   float inv_rmin, inv_log2q;
+  int select_uniform;  // 1: medium chosen uniformly, weight K w_k / sum(w)
 };
 
 enum Event : int { EV_CONTINUE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_DEAD = 3, EV_TRUNC = 4 };
@@ -123,6 +124,32 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// The flush-to-zero forms of the other hardware approximations: the same
+// results for normal operands and results (the only kind the walk produces),
+// without the compiler's rescaling around them for subnormal ones.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float div_approx(float a, float b) {
+  float y;
+  asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+  return y;
+}
+__device__ __forceinline__ void sincos_approx(float x, float* sp, float* cp) {
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*sp) : "f"(x));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*cp) : "f"(x));
+}
+
+// Paired binary32 arithmetic (one instruction for two lanes' worth of
+// values); each half is rounded exactly like the scalar __f*_rn operation.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // Unpolarised Fresnel reflectance, medium (index n) -> outside (index 1),
 // without branches: total internal reflection (n sin_i >= 1) and n = 1 are
@@ -131,12 +158,12 @@ __device__ __forceinline__ float fresnel(float cos_i, float n) {
   const float sin2_i = fmaxf(0.0f, __fmaf_rn(-cos_i, cos_i, 1.0f));
   const float sin_t = __fmul_rn(n, sqrt_approx(sin2_i));
   const float cos_t = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-sin_t, sin_t, 1.0f)));
-  const float nci = __fmul_rn(n, cos_i);
-  const float nct = __fmul_rn(n, cos_t);
-  const float sd = __fadd_rn(nci, cos_t), pd = __fadd_rn(cos_i, nct);
-  const float inv = rcp_approx(__fmul_rn(sd, pd));
-  const float rs = __fmul_rn(__fmul_rn(__fsub_rn(nci, cos_t), pd), inv);
-  const float rp = __fmul_rn(__fmul_rn(__fsub_rn(cos_i, nct), sd), inv);
+  const float2 nc = __fmul2_rn(f2(n, n), f2(cos_i, cos_t));  // (n cos_i, n cos_t)
+  const float2 sp = __fadd2_rn(f2(nc.x, cos_i), f2(cos_t, nc.y));  // (sd, pd)
+  const float inv = rcp_approx(__fmul_rn(sp.x, sp.y));
+  const float2 df = __fadd2_rn(f2(nc.x, cos_i), f2(-cos_t, -nc.y));
+  const float2 rr = __fmul2_rn(__fmul2_rn(df, f2(sp.y, sp.x)), f2(inv, inv));
+  const float rs = rr.x, rp = rr.y;
   float F = __fmul_rn(0.5f, __fmaf_rn(rs, rs, __fmul_rn(rp, rp)));
   F = sin_t >= 1.0f ? 1.0f : F;
   return n == 1.0f ? 0.0f : F;
@@ -167,7 +194,19 @@ template <bool LAYERED = false>
 __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uint32_t path,
                                           float d, Path& p) {
   const uint4 r = philox4x32_10_rk(make_uint4(0u, path, inst + c.inst_offset, 1u), c.rk);
-  const int k = select_medium(c, inst, u23(r.x));
+  int k;
+  float w_sel = 1.0f;  // w_k / (p_k sum(w)), the estimator weight of the choice
+  if (!c.select_uniform) {
+    k = select_medium(c, inst, u23(r.x));
+  } else {
+    // uniform choice (u K < K in binary32 for K <= 4), reweighted so the
+    // mixture of Eq. 4 is still estimated without bias
+    k = min(c.K - 1, (int)__fmul_rn(u23(r.x), (float)c.K));
+    float total = 0.0f;
+    for (int j = 0; j < c.K; ++j) total = __fadd_rn(total, __ldg(c.w + (size_t)j * c.n_inst + inst));
+    w_sel = __fmul_rn(__fmul_rn((float)c.K, __ldg(c.w + (size_t)k * c.n_inst + inst)),
+                      __fdiv_rn(1.0f, total));
+  }
   const size_t off = (size_t)k * c.n_inst + inst;
   p.k = k;
   p.alpha = __ldg(c.alpha + off);
@@ -177,20 +216,20 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.d = d;
   p.x = 0.0f; p.y = 0.0f; p.z = 0.0f;
   p.ux = 0.0f; p.uy = 0.0f; p.uz = 1.0f;
-  p.W = c.W0;
+  p.W = __fmul_rn(c.W0, w_sel);
   if (c.incidence == 1) {
     // cosine-weighted incident lobe: outside cosine sqrt(u), azimuth 2 pi u',
     // refracted by Snell's law; entry weight 1 - F at the refracted angle
     const uint4 e = philox4x32_10_rk(make_uint4(0u, path, inst + c.inst_offset, 2u), c.rk);
     const float mu_o = sqrt_approx(u23(e.x));
-    const float sin_i = __fdividef(sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu_o, mu_o, 1.0f))),
+    const float sin_i = div_approx(sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu_o, mu_o, 1.0f))),
                                    c.n_rel);
     float sp, cp;
-    __sincosf(__fmul_rn(6.2831853071795865f, __fsub_rn(u23(e.y), 0.5f)), &sp, &cp);
+    sincos_approx(__fmul_rn(6.2831853071795865f, __fsub_rn(u23(e.y), 0.5f)), &sp, &cp);
     p.ux = -__fmul_rn(sin_i, cp);
     p.uy = -__fmul_rn(sin_i, sp);
     p.uz = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-sin_i, sin_i, 1.0f)));
-    p.W = c.entry_fresnel ? __fsub_rn(1.0f, fresnel(p.uz, c.n_rel)) : 1.0f;
+    p.W = __fmul_rn(c.entry_fresnel ? __fsub_rn(1.0f, fresnel(p.uz, c.n_rel)) : 1.0f, w_sel);
   }
   p.Aacc = 0.0f;
   p.step = 0u;
@@ -223,7 +262,7 @@ __device__ __forceinline__ float hg_mu(float g, float u) {
   const float a = __fmaf_rn(g, __fmul_rn(xi, xi), __fmul_rn(2.0f, xi));  // 2 xi + g xi^2
   const float num = __fmaf_rn(__fadd_rn(1.0f, g2), a, __fmul_rn(g, __fsub_rn(3.0f, g2)));
   const float den = __fmaf_rn(g, xi, 1.0f);
-  const float mu = __fdividef(num, __fmul_rn(2.0f, __fmul_rn(den, den)));
+  const float mu = div_approx(num, __fmul_rn(2.0f, __fmul_rn(den, den)));
   return fminf(1.0f, fmaxf(-1.0f, mu));
 }
 
@@ -248,7 +287,7 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
 
   // Exponential free flight -ln(u0) / sigma_t, from the hardware log2
   // (absolute error <= 2^-22 mean free paths near u0 = 1, 2 ulp elsewhere).
-  const float s = fmaxf(0.0f, __fmul_rn(-__log2f(u0), p.fl));
+  const float s = fmaxf(0.0f, __fmul_rn(-lg2_approx(u0), p.fl));
   // Distance to the face the path is heading to.
   const float iuz = rcp_approx(p.uz);
   const float inf = __int_as_float(0x7f800000);
@@ -267,8 +306,9 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
   const bool hit = db <= s;
   if (LAYERED) cross = hit && (top == (p.layer == 1));
   const float dist = hit ? db : s;
-  p.x = __fmaf_rn(dist, p.ux, p.x);
-  p.y = __fmaf_rn(dist, p.uy, p.y);
+  const float2 xy = __ffma2_rn(f2(dist, dist), f2(p.ux, p.uy), f2(p.x, p.y));
+  p.x = xy.x;
+  p.y = xy.y;
   p.z = hit ? (cross ? p.d1 : (top ? 0.0f : p.d)) : __fmaf_rn(dist, p.uz, p.z);
   if (ADJ) p.L = __fadd_rn(p.L, dist);
 
@@ -296,28 +336,30 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
   if (ADJ) p.G = (hit || dead) ? p.G : __fadd_rn(p.G, hg_dlogp_dg(p.g, mu));
   // Azimuth phi = 2 pi u2; evaluated as phi - pi in (-pi, pi), then negated.
   float sp, cp;
-  __sincosf(__fmul_rn(6.2831853071795865f, __fsub_rn(u2, 0.5f)), &sp, &cp);
+  sincos_approx(__fmul_rn(6.2831853071795865f, __fsub_rn(u2, 0.5f)), &sp, &cp);
   sp = -sp;
   cp = -cp;
   const float st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
   const float s2 = __fmaf_rn(-p.uz, p.uz, 1.0f);
-  const float itmp = rsqrtf(s2);
+  const float itmp = rsqrt_approx(s2);
   const float tmp = __fmul_rn(s2, itmp);
   const float sti = __fmul_rn(st, itmp);
   const float uzcp = __fmul_rn(p.uz, cp);
   const bool polar = fabsf(p.uz) > 0.999999f;
-  const float nx = polar ? __fmul_rn(st, cp)
-                         : __fmaf_rn(sti, __fmaf_rn(p.ux, uzcp, -__fmul_rn(p.uy, sp)),
-                                     __fmul_rn(p.ux, mu));
-  const float ny = polar ? __fmul_rn(st, sp)
-                         : __fmaf_rn(sti, __fmaf_rn(p.uy, uzcp, __fmul_rn(p.ux, sp)),
-                                     __fmul_rn(p.uy, mu));
+  // (nx, ny) off the pole: sti (u_xy uz cp -+ u_yx sp) + u_xy mu, in pairs
+  const float2 cross_sp = __fmul2_rn(f2(-p.uy, p.ux), f2(sp, sp));
+  const float2 inner = __ffma2_rn(f2(p.ux, p.uy), f2(uzcp, uzcp), cross_sp);
+  const float2 nxy = __ffma2_rn(f2(sti, sti), inner, __fmul2_rn(f2(p.ux, p.uy), f2(mu, mu)));
+  const float2 pxy = __fmul2_rn(f2(st, st), f2(cp, sp));
+  const float nx = polar ? pxy.x : nxy.x;
+  const float ny = polar ? pxy.y : nxy.y;
   const float nz = polar ? (p.uz >= 0.0f ? mu : -mu)
-                         : __fmaf_rn(-__fmul_rn(st, cp), tmp, __fmul_rn(p.uz, mu));
-  const float inr = rsqrtf(__fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz))));
+                         : __fmaf_rn(-pxy.x, tmp, __fmul_rn(p.uz, mu));
+  const float inr = rsqrt_approx(__fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz))));
+  const float2 uxy = __fmul2_rn(f2(nx, ny), f2(inr, inr));
   const float uz_new = hit ? (reflect ? -p.uz : p.uz) : __fmul_rn(nz, inr);
-  p.ux = hit ? p.ux : __fmul_rn(nx, inr);
-  p.uy = hit ? p.uy : __fmul_rn(ny, inr);
+  p.ux = hit ? p.ux : uxy.x;
+  p.uy = hit ? p.uy : uxy.y;
   p.uz = uz_new;
 
   if (LAYERED && cross) {  // continue in the other layer with a fresh flight
@@ -340,7 +382,7 @@ __device__ __forceinline__ int exit_bin(const WalkConst& c, const Path& p) {
   if (!c.log_bins) return (int)fminf(floorf(__fmul_rn(rr, c.bin_scale)), (float)c.nbins);
   const float t = __fmul_rn(rr, c.inv_rmin);
   if (t < 1.0f) return 0;
-  return (int)fminf(1.0f + floorf(__fmul_rn(__log2f(t), c.inv_log2q)), (float)c.nbins);
+  return (int)fminf(1.0f + floorf(__fmul_rn(lg2_approx(t), c.inv_log2q)), (float)c.nbins);
 }
 
 }  // namespace sss

@@ -198,35 +198,46 @@ __device__ __forceinline__ int grad_exponent(const WalkConst& c, const GradIn& g
 }
 
 // Warp-uniform state of one work unit held by a warp (kept in shared memory).
+// `gen` counts the flushes of a slot: a lane whose path outlives its unit
+// (the slot was flushed, and perhaps refilled, meanwhile) sees another gen.
 struct SlotMeta {
   uint32_t inst, next, end, live;
   float d, scale, lim, wsum;
+  uint32_t gen, pad0, pad1, pad2;
 };
+static_assert(sizeof(SlotMeta) == kSlotMetaBytes, "slot header size");
 
 enum : int { LANE_IDLE = 0, LANE_RUNNING = 1, LANE_DONE = 2 };
 
-// Adds one finished path to its slot's shared accumulators.
+// Adds one finished path to its slot's shared accumulators, or, when the
+// slot has moved on to another unit (`direct`), straight to the instance's
+// global accumulators in the layout the slot flush uses.
 template <bool ADJ>
 __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& s,
-                                           const GradIn& gi, const Path& p, int ev,
-                                           unsigned long long* m) {
+                                           const GradIn& gi, const TallyOut& t, const Path& p,
+                                           int ev, unsigned long long* m, bool direct) {
+  auto add = [&](int j, unsigned long long v) {
+    if (!direct) atomicAdd(m + j, v);
+    else if (ADJ) atomicAdd(t.raw + (size_t)j * c.n_inst + p.inst, v);
+    else atomicAdd(t.raw + (size_t)p.inst * s.slot_words + j, v);
+  };
   if (!ADJ) {
     const int nb = c.nbins;
     if (ev == EV_TOP) {
       const int bin = exit_bin(c, p);
       const unsigned long long q = __float2ull_rn(__fmul_rn(p.W, kFix));
-      atomicAdd(m + bin, q);
-      atomicAdd(m + nb + 1 + p.k, q);
-      if (p.n_coll == 1u) atomicAdd(m + nb + 1 + c.K, q);
+      add(bin, q);
+      add(nb + 1 + p.k, q);
+      if (p.n_coll == 1u) add(nb + 1 + c.K, q);
       if (s.want_sumsq)
-        atomicAdd(m + nb + 6 + c.K + bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
+        add(nb + 6 + c.K + bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
     } else if (ev == EV_BOTTOM) {
-      atomicAdd(m + nb + 2 + c.K, __float2ull_rn(__fmul_rn(p.W, kFix)));
+      add(nb + 2 + c.K, __float2ull_rn(__fmul_rn(p.W, kFix)));
     } else if (ev == EV_TRUNC) {
-      atomicAdd(m + nb + 4 + c.K, 1ull);
+      add(nb + 4 + c.K, 1ull);
     }
-    if (p.Aacc > 0.0f) atomicAdd(m + nb + 3 + c.K, __float2ull_rn(__fmul_rn(p.Aacc, kFix)));
-    atomicAdd(m + nb + 5 + c.K, (unsigned long long)p.step);
+    if (p.Aacc > 0.0f) add(nb + 3 + c.K, __float2ull_rn(__fmul_rn(p.Aacc, kFix)));
+    add(nb + 5 + c.K, (unsigned long long)p.step);
   } else {
     float v = 0.0f;
     if (ev == EV_TOP) {
@@ -239,7 +250,7 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
     } else if (ev == EV_BOTTOM) {
       if (gi.grad_T) v = (float)gi.grad_T[p.inst];
     }
-    if (v != 0.0f) {
+    if (v != 0.0f && p.W != 0.0f) {  // (W = 0: a zero-weight medium, chosen uniformly)
       const float Wv = __fmul_rn(__fmul_rn(p.W, v), p.gscale);
       const float nf = (float)p.n_coll;
       float q[4];
@@ -254,15 +265,17 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
           atomicOr(s.status, SSS_DEV_FLAG_OVERFLOW);
           x = (x != x) ? 0.0f : copysignf(p.glim, x);
         }
-        atomicAdd(m + j * c.K + p.k, (unsigned long long)__float2ll_rn(x));
+        add(j * c.K + p.k, (unsigned long long)__float2ll_rn(x));
       }
     }
   }
   if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
 }
 
+// The forward one-layer kernel is held to 48 registers: five 256-thread
+// blocks per SM (40 warps) keep the issue slots busy.
 template <bool ADJ, bool LAYERED>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (ADJ || LAYERED) ? 4 : 5)
 walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   extern __shared__ unsigned long long smem[];
   const int lane = threadIdx.x & 31;
@@ -273,7 +286,10 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   SlotMeta* meta =
       reinterpret_cast<SlotMeta*>(smem + (size_t)nwarps * 2 * slot_words) + 2 * wib;
   for (int j = lane; j < 2 * slot_words; j += 32) slot_mem[j] = 0ull;
-  if (lane < 2) meta[lane].live = 0u;
+  if (lane < 2) {
+    meta[lane].live = 0u;
+    meta[lane].gen = 0u;
+  }
   __syncwarp();
 
   int cur = 0;        // slot new paths are drawn from (warp-uniform)
@@ -281,6 +297,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
 
   int st = LANE_IDLE;
   int myslot = 0;
+  uint32_t mygen = 0;
   int ev = EV_CONTINUE;
   Path p;
   p.step = 0;
@@ -313,6 +330,8 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
       sm.scale = scale;
       sm.lim = lim;
       sm.wsum = wsum;
+      sm.gen = meta[o].gen;
+      sm.pad0 = sm.pad1 = sm.pad2 = 0u;
       meta[o] = sm;
     }
     __syncwarp();
@@ -333,7 +352,10 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
       }
     }
     __syncwarp();
-    if (lane == 0) meta[o].live = 0u;
+    if (lane == 0) {
+      meta[o].live = 0u;
+      meta[o].gen += 1u;  // paths of the flushed unit now tally directly
+    }
     __syncwarp();
   };
 
@@ -345,7 +367,8 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     if (n_nr >= s.regroup || n_nr == 32) {
       // ---- 1. finished lanes tally together (one divergent block) ----
       if (st == LANE_DONE) {
-        tally_path<ADJ>(c, s, gi, p, ev, slot_mem + (size_t)myslot * slot_words);
+        tally_path<ADJ>(c, s, gi, t, p, ev, slot_mem + (size_t)myslot * slot_words,
+                        meta[myslot].gen != mygen);
         st = LANE_IDLE;
       }
       // ---- 2. refill idle lanes from the current unit (regrouping) ----
@@ -365,6 +388,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
             }
             st = LANE_RUNNING;
             myslot = cur;
+            mygen = meta[cur].gen;
           }
           __syncwarp();
           if (lane == 0) meta[cur].next = nxt + take;
@@ -372,11 +396,10 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
           idle = __ballot_sync(kFull, st == LANE_IDLE);
         } else {
           if (!more) break;
+          // The other slot is reused at once: its partial sums go to global
+          // memory, and its paths still running tally there directly.
           const int o = cur ^ 1;
-          if (meta[o].live) {
-            if (__ballot_sync(kFull, st == LANE_RUNNING && myslot == o) != 0u) break;
-            flush(o);
-          }
+          if (meta[o].live) flush(o);
           if (!fetch(o)) {
             more = false;
             break;
@@ -384,10 +407,11 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
           cur = o;
         }
       }
-    }
-    if (__ballot_sync(kFull, st == LANE_RUNNING) == 0u) {
-      if (!more) break;
-      continue;
+      // (without a refill fewer than `regroup` lanes are idle, so some run)
+      if (__ballot_sync(kFull, st == LANE_RUNNING) == 0u) {
+        if (!more) break;
+        continue;
+      }
     }
     // ---- advance every running path by one draw ----
     if (st == LANE_RUNNING) {

@@ -16,6 +16,10 @@ enum : unsigned int {
   SSS_DEV_FLAG_ZERO_WEIGHT = 0x8u,
 };
 
+// Bytes of the per-slot header (SlotMeta) after a warp's two slots of
+// shared accumulators.
+constexpr int kSlotMetaBytes = 48;
+
 struct WalkSched {
   unsigned long long* unit_counter;      // global work-queue head (zeroed per call)
   const unsigned long long* prefix;      // [n_inst+1] unit prefix, or null (uniform)
@@ -23,7 +27,6 @@ struct WalkSched {
   unsigned long long units_per_inst;     // uniform budgets only
   uint32_t unit_paths;                   // paths per unit
   int regroup;                           // refill when this many lanes are idle
-  int burst;                             // draws per lane between refill checks
   int slot_words;                        // uint64 words per slot (tallies or grads)
   int want_sumsq;
   unsigned int* status;

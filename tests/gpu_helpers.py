@@ -10,7 +10,8 @@ def to_oracle_opts(o):
                              rr_threshold=o.rr_threshold, entry_fresnel=o.entry_fresnel,
                              max_steps=o.max_steps, seed=o.seed,
                              incidence=getattr(o, "incidence", 0),
-                             log_r_min_mm=getattr(o, "log_r_min_mm", 0.0))
+                             log_r_min_mm=getattr(o, "log_r_min_mm", 0.0),
+                             select_pdf=getattr(o, "select_pdf", 0))
 
 
 def run_gpu(x, o, raw=False, media=None):

@@ -44,9 +44,12 @@ def _upstream(x, nbins, seed=0):
                 grad_R_k=rng.normal(size=(n, x.K)))
 
 
-def test_adjoint_matches_oracle_score_gradient(api):
+@pytest.mark.parametrize("select_pdf", [0, 1])
+def test_adjoint_matches_oracle_score_gradient(api, select_pdf):
+    # select_pdf = 1: uniform medium choice, whose weight K w_k / sum(w)
+    # rides on the path weight, so the same score terms apply
     x = inputs.spectral_field(n_texels=3, param_seed=3, n_paths=8192)
-    o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1003)
+    o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1003, select_pdf=select_pdf)
     up = _upstream(x, 64)
     g, code, flags = _grads_gpu(api, x, o, **up)
     assert code == 0 and flags == 0

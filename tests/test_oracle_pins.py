@@ -351,6 +351,38 @@ def _layer2(a, s, g, d1, n=1):
     return (f(a), f(s), f(g), f(d1))
 
 
+def test_uniform_selection_pdf_is_unbiased():
+    # another selection pdf (Sec. 7): uniform choice reweighted by
+    # K w_k / sum(w) estimates the same mixture (Eq. 4) as choosing by w_k;
+    # unnormalised weights catch a missing 1/sum(w), a missing K, or a
+    # weight applied to the wrong medium.
+    a = np.array([[0.99], [0.8], [0.95]], np.float32)
+    s = np.array([[1.0], [5.0], [2.0]], np.float32)
+    g = np.array([[0.8], [0.0], [0.5]], np.float32)
+    w = np.array([[2.0], [0.5], [1.0]], np.float32)
+    N = np.array([1 << 17], np.uint32)
+    byw = oracle.walk(a, s, g, w, N, None, 1.4, oracle.OracleOpts(nbins=8, r_max_mm=4.0, seed=21))
+    uni = oracle.walk(a, s, g, w, N, None, 1.4,
+                      oracle.OracleOpts(nbins=8, r_max_mm=4.0, seed=22, select_pdf=1))
+    for key in ("R", "T", "A", "R1"):
+        assert abs(uni[key][0] - byw[key][0]) <= Z * np.hypot(uni["se_" + key][0],
+                                                               byw["se_" + key][0]), key
+    d = np.abs(uni["R_k"][0] - byw["R_k"][0])
+    assert np.all(d <= Z * np.hypot(uni["se_R_k"][0], byw["se_R_k"][0]))
+    assert np.all(np.abs(uni["bins"][0] - byw["bins"][0])
+                  <= Z * np.hypot(uni["se_bins"][0], byw["se_bins"][0]) + 1e-12)
+    # a zero-weight medium is still walked but carries nothing, and its
+    # gradient stays finite
+    w0 = np.array([[1.0], [0.0], [1.0]], np.float32)
+    z = oracle.walk(a, s, g, w0, np.array([20000], np.uint32), None, 1.4,
+                    oracle.OracleOpts(nbins=8, r_max_mm=4.0, seed=23, select_pdf=1))
+    assert z["R_k"][0, 1] == 0.0 and z["R_k"][0, 0] > 0.0
+    gz = oracle.walk_grad(a, s, g, w0, np.array([20000], np.uint32), None, 1.4,
+                          oracle.OracleOpts(nbins=8, r_max_mm=4.0, seed=23, select_pdf=1),
+                          grad_R=np.ones(1))
+    assert np.all(np.isfinite(gz["d_w"])) and gz["d_w"][1, 0] == 0.0
+
+
 def test_log_bins_partition_the_same_exits():
     # logarithmic bins (512 to 50 mm, as the paper's generator) regroup the
     # same exits: their sum equals the linear bins' sum plus overflow, and a

@@ -130,6 +130,25 @@ def test_log_radial_bins_parity(api):
     np.testing.assert_array_equal(exits_log, exits_lin)
 
 
+def test_uniform_selection_pdf_parity(api):
+    # uniform medium choice reweighted by K w_k / sum(w) (Sec. 7 leaves the
+    # selection pdf open): same-stream parity with the oracle, and the same
+    # mixture as choosing by w_k within the statistical bar
+    x = inputs.spectral_field(n_texels=4, param_seed=9, n_paths=8192)
+    o = opts(api, nbins=32, r_max_mm=10.0, seed=55, select_pdf=1)
+    g, code, flags = run_gpu(x, o)
+    assert code == 0 and flags == 0
+    r = run_oracle(x, o)
+    worst, where = compare_same_stream(g, r, x.n_paths, r["steps"])
+    print("uniform-selection same-stream worst ratio", worst, where)
+    assert worst <= 1.0, where
+    gw, _, _ = run_gpu(x, opts(api, nbins=32, r_max_mm=10.0, seed=56))
+    z = (g["R"] - gw["R"]) / np.hypot(g["stderr_R"], gw["stderr_R"])
+    assert np.all(np.abs(z) <= 5.0)
+    print("uniform vs by-weight R: z rms", np.sqrt(np.mean(z ** 2)))
+    assert np.sqrt(np.mean(z ** 2)) < 1.3
+
+
 def test_two_layer_slab_parity_and_limits(api):
     # skin-like two-layer slabs: same-stream parity with the oracle, the
     # plain baseline bit-identical, and a top layer too thick to cross
