@@ -13,9 +13,11 @@ Citations are to the paper's sections and equations:
   * Sec. 7: the medium is drawn with probability w_k at the walk start.
 """
 from .walk import (OracleOpts, philox4x32_10, fresnel, hg_mu, hg_dlogp_dg, rotate,
-                   select_medium, walk, walk_grad, trace, num_threads, PATH_DTYPE)
+                   select_medium, walk, walk_grad, walk_hero, trace, num_threads,
+                   PATH_DTYPE)
 from . import hfunction
 
 __all__ = ["OracleOpts", "philox4x32_10", "fresnel", "hg_mu", "hg_dlogp_dg", "rotate",
-           "select_medium", "walk", "walk_grad", "trace", "num_threads", "PATH_DTYPE",
+           "select_medium", "walk", "walk_grad", "walk_hero", "trace", "num_threads",
+           "PATH_DTYPE",
            "hfunction"]

@@ -181,6 +181,37 @@ def walk(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
     return res
 
 
+def walk_hero(alpha, sigma_t, g, w, n_paths_per_group: int, hero: int, bands_per_texel: int,
+              thickness_mm=None, n_rel=1.0, opts: OracleOpts = OracleOpts(),
+              inst_offset: int = 0, orbits: bool = False) -> dict:
+    """Hero-wavelength walk (see ``oracle_walk_hero`` in ``walk_oracle.c``):
+    instances are texels x ``bands_per_texel`` bands, band fastest; each group
+    of ``hero`` bands (adjacent, or with ``orbits`` the rotation orbits of
+    stride bands_per_texel / hero) shares ``n_paths_per_group`` path
+    geometries, each member scoring the balance-heuristic estimate.  Returns the same per-instance dict as
+    ``walk`` (A and se_A are 0)."""
+    alpha, sigma_t, g, w, K, n = _check(alpha, sigma_t, g, w)
+    th = None if thickness_mm is None else _f32(thickness_mm)
+    nb = opts.nbins
+    res = {k: np.zeros(n) for k in ("R", "T", "A", "overflow", "R1", "truncated",
+                                    "se_R", "se_T", "se_A", "se_R1", "steps")}
+    res["bins"] = np.zeros((n, nb))
+    res["se_bins"] = np.zeros((n, nb))
+    res["R_k"] = np.zeros((n, K))
+    res["se_R_k"] = np.zeros((n, K))
+    out = _Out(**{k: _p(v) for k, v in res.items()})
+    o = opts._c()
+    rc = _load().oracle_walk_hero(C.c_int64(n), C.c_int(K), _p(alpha), _p(sigma_t), _p(g),
+                                  _p(w), C.c_uint32(n_paths_per_group), _p(th),
+                                  C.c_double(n_rel), C.byref(o), C.c_int(hero),
+                                  C.c_int(bands_per_texel), C.c_int(int(orbits)),
+                                  C.c_uint32(inst_offset),
+                                  C.byref(out))
+    if rc != 0:
+        raise ValueError("oracle_walk_hero rejected its arguments")
+    return res
+
+
 def walk_grad(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
               opts: OracleOpts = OracleOpts(), grad_R=None, grad_bins=None,
               grad_R_k=None, grad_T=None, inst_ids=None) -> dict:

@@ -454,6 +454,238 @@ int oracle_walk(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Hero-wavelength walk: one path geometry shared by C bands of a texel.      */
+/* ------------------------------------------------------------------------ */
+/* Hero-wavelength spectral sampling (Wilkie et al., EGSR 2014; the paper's
+ * related work names hero-wavelength tracking), applied to the mixture walk.
+ * Instances are texels x nb bands, band fastest.  With C dividing nb, the
+ * bands of a texel fall into nb/C groups whose members share path
+ * geometries: blocks of C adjacent bands, or (orbits = 1) Wilkie et al.'s
+ * rotation orbits {o, o + nb/C, ..., o + (C-1) nb/C}.  The estimate is
+ * unbiased for any partition, since given its group a path's hero is
+ * uniform over the members; adjacent bands have close optics, so their
+ * balance weights stay near 1/C and the variance near that of separate
+ * walks.  Path p of a
+ * group samples everything (medium choice, flights, Henyey-Greenstein
+ * cosines, roulette) with the optics of its hero member h = p mod C, so each
+ * member is the hero of N/C of the paths.  Member j then scores the
+ * one-sample balance-heuristic estimate
+ *     F_j = f_j(x) / ((1/C) sum_i p_i(x)) = W_j C / sum_i exp(L_i - L_j),
+ * where p_i is the density of the path's sampling decisions under member i's
+ * optics (selection probability of the chosen medium, exp(-sigma s) and
+ * sigma per collision, p_HG(mu) per scattering; Fresnel choices are the same
+ * for every member and cancel), L_i = log p_i, and W_j = f_j / p_j is the
+ * member's albedo-weighted throughput (entry weight, w_k / selection
+ * probability, alpha_j per collision, and the roulette boosts, which depend
+ * on the hero's weight only and are shared).  Weight mode only; absorption
+ * (A) is not scored.  Counters: (step, path, first member + offset, tag). */
+static double hg_logpdf(double g, double mu) {
+  /* density of mu = cos(theta) on [-1, 1] */
+  return log(0.5 * (1.0 - g * g)) - 1.5 * log(1.0 + g * g - 2.0 * g * mu);
+}
+
+typedef struct {
+  int exit_kind;          /* 0 top, 1 bottom, 2 roulette, 3 truncated */
+  int medium, bin;
+  uint32_t steps, n_coll;
+  double F[ORC_KMAX];     /* per member: the balance-heuristic exit weight */
+} oracle_hero_path;
+
+static void trace_hero(const float* alpha, const float* sigma_t, const float* g, const float* w,
+                       int K, int64_t n_inst, const int64_t* mem, int C, int h,
+                       uint32_t rng_inst, uint32_t path, double d, double n_rel,
+                       const oracle_opts* o, oracle_hero_path* res) {
+  double u[4];
+  memset(res, 0, sizeof(*res));
+  float wk[ORC_KMAX];
+  for (int k = 0; k < K; ++k) wk[k] = w[(int64_t)k * n_inst + mem[h]];
+  draw4(o->seed, 0u, path, rng_inst, 1u, u);
+  int k;
+  if (o->select_pdf == 1) {
+    k = (int)floor(u[0] * (double)K);
+    if (k > K - 1) k = K - 1;
+  } else {
+    k = oracle_select_medium(wk, K, u[0]);
+  }
+  res->medium = k;
+  double a[ORC_KMAX], st[ORC_KMAX], gg[ORC_KMAX], L[ORC_KMAX], W[ORC_KMAX];
+  for (int i = 0; i < C; ++i) {
+    a[i] = alpha[(int64_t)k * n_inst + mem[i]];
+    st[i] = sigma_t[(int64_t)k * n_inst + mem[i]];
+    gg[i] = g[(int64_t)k * n_inst + mem[i]];
+    double tot = 0.0;
+    for (int j = 0; j < K; ++j) tot += (double)w[(int64_t)j * n_inst + mem[i]];
+    const double mix = (double)w[(int64_t)k * n_inst + mem[i]] / tot; /* Eq. 4 weight */
+    const double sel = o->select_pdf == 1 ? 1.0 / (double)K : mix; /* its choice prob. */
+    L[i] = log(sel);
+    W[i] = mix / sel;
+  }
+  double pos[3] = {0.0, 0.0, 0.0};
+  double dir[3] = {0.0, 0.0, 1.0};
+  if (o->incidence == 1) {
+    double v[4];
+    draw4(o->seed, 0u, path, rng_inst, 2u, v);
+    const double mu_o = sqrt(v[0]);
+    const double sin_i = sqrt(fmax(0.0, 1.0 - mu_o * mu_o)) / n_rel;
+    const double phi = 2.0 * M_PI * v[1];
+    dir[0] = sin_i * cos(phi);
+    dir[1] = sin_i * sin(phi);
+    dir[2] = sqrt(1.0 - sin_i * sin_i);
+  }
+  const double W0 = o->entry_fresnel ? 1.0 - oracle_fresnel(dir[2], n_rel) : 1.0;
+  for (int i = 0; i < C; ++i) W[i] *= W0;
+
+  uint32_t step = 0;
+  for (;;) {
+    if (step >= o->max_steps) { res->exit_kind = 3; break; }
+    draw4(o->seed, step, path, rng_inst, 0u, u);
+    step++;
+    const double s = -log(u[0]) / st[h];
+    double db = INFINITY;
+    if (dir[2] < 0.0) db = -pos[2] / dir[2];
+    else if (dir[2] > 0.0) db = (d - pos[2]) / dir[2];
+    if (db <= s) {
+      /* no collision over db: probability exp(-sigma db) under each member */
+      for (int i = 0; i < C; ++i) L[i] += -st[i] * db;
+      pos[0] += db * dir[0];
+      pos[1] += db * dir[1];
+      const int top = dir[2] < 0.0;
+      pos[2] = top ? 0.0 : d;
+      const double F = oracle_fresnel(fabs(dir[2]), n_rel);
+      if (u[1] < F) { dir[2] = -dir[2]; continue; }
+      res->exit_kind = top ? 0 : 1;
+      if (top) {
+        const double r = sqrt(pos[0] * pos[0] + pos[1] * pos[1]);
+        double fb;
+        if (o->log_r_min_mm > 0.0) {
+          fb = r < o->log_r_min_mm
+                   ? 0.0
+                   : 1.0 + floor(log(r / o->log_r_min_mm) /
+                                 (log(o->r_max_mm / o->log_r_min_mm) / (o->nbins - 1)));
+        } else {
+          fb = floor(r * (double)o->nbins / o->r_max_mm);
+        }
+        res->bin = fb >= (double)o->nbins ? o->nbins : (int)fb;
+      }
+      for (int j = 0; j < C; ++j) {
+        double den = 0.0;
+        for (int i = 0; i < C; ++i) den += exp(L[i] - L[j]);
+        res->F[j] = W[j] * (double)C / den;
+      }
+      break;
+    }
+    /* collision after s: density sigma exp(-sigma s) under each member */
+    for (int i = 0; i < C; ++i) L[i] += log(st[i]) - st[i] * s;
+    for (int i = 0; i < 3; ++i) pos[i] += s * dir[i];
+    res->n_coll++;
+    for (int i = 0; i < C; ++i) W[i] *= a[i];
+    if (W[h] < o->rr_threshold) {
+      /* roulette on the hero's weight; survivors of every member are
+       * boosted by the same factor */
+      if (u[3] < W[h] / o->rr_threshold) {
+        const double boost = o->rr_threshold / W[h];
+        for (int i = 0; i < C; ++i) W[i] = i == h ? o->rr_threshold : W[i] * boost;
+      } else {
+        res->exit_kind = 2;
+        break;
+      }
+    }
+    const double mu = oracle_hg_mu(gg[h], u[1]);
+    for (int i = 0; i < C; ++i) L[i] += hg_logpdf(gg[i], mu);
+    oracle_rotate(dir, mu, 2.0 * M_PI * u[2]);
+  }
+  res->steps = step;
+}
+
+/* Tallies per member instance, as oracle_walk's (A and se_A stay 0).
+ * N paths per group; thickness_mm (or NULL) is read at each group's first
+ * member and shared by the group. */
+int oracle_walk_hero(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
+                     const float* g, const float* w, uint32_t N, const float* thickness_mm,
+                     double n_rel, const oracle_opts* o, int C, int nb_texel, int orbits,
+                     uint32_t inst_offset, oracle_out* out) {
+  if (K < 1 || K > ORC_KMAX || o->nbins < 1 || o->nbins > ORC_NBINS_MAX) return 1;
+  if (C < 1 || C > ORC_KMAX || nb_texel < C || nb_texel % C || n_inst % nb_texel) return 1;
+  if (o->mode != 0) return 1;
+  const int nb = o->nbins;
+  const int nv = nb + 1 + K + 4; /* [bins][overflow][R_k][R1][T][trunc][steps] */
+  const int64_t per_texel = nb_texel / C;  /* groups per texel */
+  const int64_t n_groups = n_inst / C;
+  for (int64_t grp = 0; grp < n_groups; ++grp) {
+    /* orbits: {q, q + nb/C, ...}; otherwise blocks of C adjacent bands */
+    const int64_t q = grp % per_texel;
+    const int64_t stride = orbits ? per_texel : 1;
+    const int64_t first = (grp / per_texel) * nb_texel + (orbits ? q : q * C);
+    int64_t mem[ORC_KMAX];
+    for (int j = 0; j < C; ++j) mem[j] = first + j * stride;
+    const double d = thickness_mm ? (double)thickness_mm[first] : INFINITY;
+    const int64_t nch = ((int64_t)N + ORC_CHUNK - 1) / ORC_CHUNK;
+    const size_t per = 2 * (size_t)nv * (size_t)C;
+    double* ps = calloc((size_t)(nch > 0 ? nch : 1) * per, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      double* ls = ps + (size_t)ch * per;  /* [C][nv] sums, then [C][nv] squares */
+      double c[ORC_NV_MAX];
+      const int64_t p1 = (ch + 1) * ORC_CHUNK < (int64_t)N ? (ch + 1) * ORC_CHUNK : (int64_t)N;
+      for (int64_t p = ch * ORC_CHUNK; p < p1; ++p) {
+        oracle_hero_path r;
+        trace_hero(alpha, sigma_t, g, w, K, n_inst, mem, C, (int)(p % C),
+                   (uint32_t)(first + inst_offset), (uint32_t)p, d, n_rel, o, &r);
+        for (int j = 0; j < C; ++j) {
+          memset(c, 0, sizeof(double) * (size_t)nv);
+          if (r.exit_kind == 0) {
+            c[r.bin] = r.F[j];
+            c[nb + 1 + r.medium] = r.F[j];
+            if (r.n_coll == 1) c[nb + 1 + K] = r.F[j];
+          } else if (r.exit_kind == 1) {
+            c[nb + 2 + K] = r.F[j];
+          } else if (r.exit_kind == 3) {
+            c[nb + 3 + K] = 1.0;
+          }
+          c[nb + 4 + K] = (double)r.steps;
+          double* lj = ls + (size_t)j * nv;
+          double* l2j = ls + (size_t)C * nv + (size_t)j * nv;
+          for (int q = 0; q < nv; ++q) { lj[q] += c[q]; l2j[q] += c[q] * c[q]; }
+        }
+      }
+    }
+    for (int j = 0; j < C; ++j) {
+      const int64_t i = mem[j];
+      double s[ORC_NV_MAX] = {0}, s2[ORC_NV_MAX] = {0};
+      for (int64_t ch = 0; ch < nch; ++ch)
+        for (int q = 0; q < nv; ++q) {
+          s[q] += ps[(size_t)ch * per + (size_t)j * nv + (size_t)q];
+          s2[q] += ps[(size_t)ch * per + (size_t)C * nv + (size_t)j * nv + (size_t)q];
+        }
+      const double n = (double)N;
+      double sR = 0.0, s2R = 0.0;
+      for (int b = 0; b <= nb; ++b) { sR += s[b]; s2R += s2[b]; }
+      if (out->R) out->R[i] = sR / n;
+      if (out->se_R) out->se_R[i] = se_of(sR, s2R, n);
+      for (int b = 0; b < nb; ++b) {
+        if (out->bins) out->bins[i * nb + b] = s[b] / n;
+        if (out->se_bins) out->se_bins[i * nb + b] = se_of(s[b], s2[b], n);
+      }
+      if (out->overflow) out->overflow[i] = s[nb] / n;
+      for (int k = 0; k < K; ++k) {
+        if (out->R_k) out->R_k[i * K + k] = s[nb + 1 + k] / n;
+        if (out->se_R_k) out->se_R_k[i * K + k] = se_of(s[nb + 1 + k], s2[nb + 1 + k], n);
+      }
+      if (out->R1) out->R1[i] = s[nb + 1 + K] / n;
+      if (out->se_R1) out->se_R1[i] = se_of(s[nb + 1 + K], s2[nb + 1 + K], n);
+      if (out->T) out->T[i] = s[nb + 2 + K] / n;
+      if (out->se_T) out->se_T[i] = se_of(s[nb + 2 + K], s2[nb + 2 + K], n);
+      if (out->A) out->A[i] = 0.0;
+      if (out->se_A) out->se_A[i] = 0.0;
+      if (out->truncated) out->truncated[i] = s[nb + 3 + K];
+      if (out->steps) out->steps[i] = s[nb + 4 + K] / n;
+    }
+    free(ps);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Score-function gradient (differentiating the path contribution f_SSS of  */
 /* Sec. 4.1 and the mixture of Eq. 4).                                        */
 /* ------------------------------------------------------------------------ */

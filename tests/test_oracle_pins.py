@@ -383,6 +383,53 @@ def test_uniform_selection_pdf_is_unbiased():
     assert np.all(np.isfinite(gz["d_w"])) and gz["d_w"][1, 0] == 0.0
 
 
+def test_hero_walk_reduces_to_the_walk_and_is_unbiased():
+    # hero-wavelength sharing (Wilkie et al. 2014; named in the paper's
+    # related work): C = 1 is the plain walk bit for bit; with C = 3, over
+    # adjacent-band groups and over rotation orbits, every band's tallies
+    # match separate per-band walks within the statistical bar.
+    from paper_2606_27604_b300 import inputs
+    x = inputs.spectral_field(n_texels=2, param_seed=3, n_paths=1)
+    o = oracle.OracleOpts(nbins=16, r_max_mm=10.0, seed=5)
+    one = oracle.walk_hero(x.alpha, x.sigma_t, x.g, x.w, 3000, 1, 81, None, x.n_rel, o)
+    ref = oracle.walk(x.alpha, x.sigma_t, x.g, x.w, np.full(x.n_inst, 3000, np.uint32), None,
+                      x.n_rel, o)
+    for key in ("R", "T", "bins", "overflow", "R_k", "R1", "steps"):
+        np.testing.assert_array_equal(one[key], ref[key])
+    N = 30000
+    sep = oracle.walk(x.alpha, x.sigma_t, x.g, x.w, np.full(x.n_inst, N, np.uint32), None,
+                      x.n_rel, oracle.OracleOpts(nbins=16, r_max_mm=10.0, seed=6))
+    for orbits in (False, True):
+        h = oracle.walk_hero(x.alpha, x.sigma_t, x.g, x.w, N, 3, 81, None, x.n_rel, o,
+                             orbits=orbits)
+        for key in ("R", "R1"):
+            z = (h[key] - sep[key]) / np.hypot(h["se_" + key], sep["se_" + key])
+            assert np.sqrt(np.mean(z ** 2)) < 1.25 and np.abs(z).max() < 4.5, (orbits, key)
+        m = (h["se_bins"] > 0) & (sep["se_bins"] > 0)
+        zb = (h["bins"] - sep["bins"])[m] / np.hypot(h["se_bins"], sep["se_bins"])[m]
+        assert np.sqrt(np.mean(zb ** 2)) < 1.25, orbits
+        if not orbits:
+            # adjacent bands: balance weights near 1/C, so one shared path per
+            # group is worth about one path per band
+            assert np.median(h["se_R"] / sep["se_R"]) < 1.1
+
+
+def test_hero_walk_identical_members_share_every_tally():
+    # members with identical optics have equal path densities, so every
+    # balance weight is 1/C and all members score exactly the same
+    a, s, g, w = _single(0.95, 3.0, 0.7, K=3, n=6, w=[[0.5] * 6, [0.3] * 6, [0.2] * 6])
+    a[1] = 0.7
+    s[2] = 9.0
+    h = oracle.walk_hero(a, s, g, w, 4000, 3, 3, None, 1.4,
+                         oracle.OracleOpts(nbins=8, r_max_mm=4.0, seed=9))
+    for key in ("R", "T", "R1", "steps"):
+        assert np.all(h[key][0:3] == h[key][0]) and np.all(h[key][3:6] == h[key][3]), key
+    np.testing.assert_array_equal(h["bins"][1], h["bins"][0])
+    one = oracle.walk(a, s, g, w, np.full(6, 60000, np.uint32), None, 1.4,
+                      oracle.OracleOpts(nbins=8, r_max_mm=4.0, seed=10))
+    assert abs(h["R"][0] - one["R"][0]) <= Z * np.hypot(h["se_R"][0], one["se_R"][0])
+
+
 def test_log_bins_partition_the_same_exits():
     # logarithmic bins (512 to 50 mm, as the paper's generator) regroup the
     # same exits: their sum equals the linear bins' sum plus overflow, and a
