@@ -316,6 +316,8 @@ def main():
     ap.add_argument("--no-baselines", action="store_true",
                     help="skip the uneven-batch and plain one-launch-per-instance timings")
     ap.add_argument("--no-decoder", action="store_true")
+    ap.add_argument("--no-hero", action="store_true",
+                    help="skip the hero-wavelength comparison")
     ap.add_argument("--pipeline", action="store_true",
                     help="run the full RGB -> decoder -> walk pipeline instead")
     ap.add_argument("--pipeline-side", type=int, default=1024)
@@ -408,6 +410,7 @@ def main():
     steps_mean = float(out["steps"].mean().item())
     total_draws = float(out["steps"].double().sum().item()) * WORKLOAD["paths_per_instance"]
     code, flags = api.read_status(wsp)
+    se_per_band = out["stderr_R"].clone()
 
     # ---- end to end through the API with host buffers ---------------------
     e2e = None
@@ -522,6 +525,39 @@ def main():
         api.release_plans()
         del wu, tu, wsb, tsb
 
+    # ---- hero-wavelength sharing: one path per group of 3 adjacent bands ---
+    hero = None
+    if not args.no_hero:
+        from dataclasses import replace as _rep
+        oh = _rep(o, hero_bands=3, hero_texel_bands=81)
+        wh = api.alloc_workspace(m, oh)
+        th_ = api.alloc_tallies(m, oh)
+        api.walk(m, oh, workspace=wh, out=th_)
+        torch.cuda.synchronize()
+        hts = []
+        for _ in range(2):
+            ha, hb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            api.profile_events(ha, hb)
+            api.walk(m, oh, workspace=wh, out=th_)
+            api.profile_events(None, None)
+            torch.cuda.synchronize()
+            hts.append(ha.elapsed_time(hb) / 1e3)
+        hcode, hflags = api.read_status(wh)
+        t_h = float(np.mean(hts))
+        t_b = float(np.mean(kern))
+        se_ratio = float(torch.median(th_["stderr_R"] / se_per_band).item())
+        n_inst = x.n_inst
+        N = WORKLOAD["paths_per_instance"]
+        hero = {"C": 3, "grouping": "blocks of 3 adjacent bands of a texel",
+                "workload": f"{WORKLOAD['workload']}, {N} paths per group",
+                "kernel_ms": t_h * 1e3, "per_band_kernel_ms": t_b * 1e3,
+                "paths_per_s": n_inst / 3 * N / t_h,
+                "band_samples_per_s": n_inst * N / t_h,
+                "stderr_R_ratio_median": se_ratio,
+                "speedup_at_equal_error": (t_b / t_h) / se_ratio ** 2,
+                "status": hcode}
+        del wh, th_
+
     # ---- decoder (RGB -> per-band mixture parameters, tensor cores) --------
     decoder = None
     if not args.no_decoder:
@@ -587,7 +623,8 @@ def main():
                            steps_per_path=steps_mean),
             "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps,
             "roofline": roofline, "cpu_baseline": cpu,
-            "adjoint_forward_ratio": ratio, "baselines": baselines, "decoder": decoder,
+            "adjoint_forward_ratio": ratio, "baselines": baselines, "hero_wavelength": hero,
+            "decoder": decoder,
             "launch_shape": {k: getattr(o, k) for k in ("block_threads", "unit_paths", "regroup")},
             "status_flags": flags}
     if rank == 0:

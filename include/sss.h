@@ -147,6 +147,25 @@ typedef struct {
  *                     multiplied by K w_k / sum(w) so the mixture of Eq. 4
  *                     is estimated without bias (Sec. 7 leaves other
  *                     choices open).  Other values: SSS_ERR_INVALID_ARG.
+ *   hero_bands      : 0 = off (default).  C in [1, 4]: hero-wavelength
+ *                     sharing (Wilkie et al. 2014; the paper's related work
+ *                     names hero-wavelength tracking).  Instances are texels
+ *                     of hero_texel_bands consecutive bands; each texel's
+ *                     bands form groups of C (blocks of C adjacent bands, or
+ *                     with hero_orbits = 1 the rotation orbits {q, q + nb/C,
+ *                     ...}).  Path p of a group samples with the optics of
+ *                     member p mod C (counters: step, p, the group's first
+ *                     member + instance_offset, tag) and every member scores
+ *                     the balance-heuristic estimate C f_j / sum_i p_i, so a
+ *                     group walks n_paths paths and each member gets an
+ *                     n_paths-sample estimate.  Roulette is decided on the
+ *                     largest member weight.  Requires mode 0, hero_texel_bands
+ *                     a multiple of C, n_inst a multiple of hero_texel_bands
+ *                     and uniform budgets (n_paths NULL), else
+ *                     SSS_ERR_INVALID_ARG; the plain schedule, the adjoint
+ *                     and two-layer slabs return SSS_ERR_UNSUPPORTED.  The
+ *                     slab thickness is the group's first member's.  A (the
+ *                     absorbed fraction) is not scored and reads 0.
  */
 typedef struct {
   int32_t nbins;
@@ -167,6 +186,9 @@ typedef struct {
   int32_t incidence;
   float log_r_min_mm;
   int32_t select_pdf;
+  int32_t hero_bands;
+  int32_t hero_texel_bands;
+  int32_t hero_orbits;
 } sss_walk_opts;
 
 /* Forward outputs, all float64 device arrays owned by the caller; any may be

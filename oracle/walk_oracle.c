@@ -476,9 +476,9 @@ int oracle_walk(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
  * sigma per collision, p_HG(mu) per scattering; Fresnel choices are the same
  * for every member and cancel), L_i = log p_i, and W_j = f_j / p_j is the
  * member's albedo-weighted throughput (entry weight, w_k / selection
- * probability, alpha_j per collision, and the roulette boosts, which depend
- * on the hero's weight only and are shared).  Weight mode only; absorption
- * (A) is not scored.  Counters: (step, path, first member + offset, tag). */
+ * probability, alpha_j per collision, and the roulette boosts, shared by the
+ * members and decided on their largest weight).  Weight mode only;
+ * absorption (A) is not scored.  Counters: (step, path, first member + offset, tag). */
 static double hg_logpdf(double g, double mu) {
   /* density of mu = cos(theta) on [-1, 1] */
   return log(0.5 * (1.0 - g * g)) - 1.5 * log(1.0 + g * g - 2.0 * g * mu);
@@ -579,12 +579,15 @@ static void trace_hero(const float* alpha, const float* sigma_t, const float* g,
     for (int i = 0; i < 3; ++i) pos[i] += s * dir[i];
     res->n_coll++;
     for (int i = 0; i < C; ++i) W[i] *= a[i];
-    if (W[h] < o->rr_threshold) {
-      /* roulette on the hero's weight; survivors of every member are
-       * boosted by the same factor */
-      if (u[3] < W[h] / o->rr_threshold) {
-        const double boost = o->rr_threshold / W[h];
-        for (int i = 0; i < C; ++i) W[i] = i == h ? o->rr_threshold : W[i] * boost;
+    /* roulette on the largest member weight Wr (survival probability > 0
+     * whenever any member still carries weight); survivors of every member
+     * are boosted by the same factor rr / Wr */
+    double Wr = 0.0;
+    for (int i = 0; i < C; ++i) Wr = fmax(Wr, W[i]);
+    if (Wr < o->rr_threshold) {
+      if (u[3] < Wr / o->rr_threshold) {
+        const double boost = o->rr_threshold / Wr;
+        for (int i = 0; i < C; ++i) W[i] = W[i] == Wr ? o->rr_threshold : W[i] * boost;
       } else {
         res->exit_kind = 2;
         break;

@@ -45,7 +45,8 @@ class Opts(C.Structure):
                 ("block_threads", C.c_int32), ("unit_paths", C.c_int32),
                 ("regroup", C.c_int32), ("instance_offset", C.c_uint32),
                 ("incidence", C.c_int32), ("log_r_min_mm", C.c_float),
-                ("select_pdf", C.c_int32)]
+                ("select_pdf", C.c_int32), ("hero_bands", C.c_int32),
+                ("hero_texel_bands", C.c_int32), ("hero_orbits", C.c_int32)]
 
 
 class Tallies(C.Structure):
@@ -141,6 +142,9 @@ class WalkOptions:
     incidence: int = 0
     log_r_min_mm: float = 0.0
     select_pdf: int = 0
+    hero_bands: int = 0
+    hero_texel_bands: int = 0
+    hero_orbits: int = 0
 
     def c(self) -> Opts:
         return Opts(**asdict(self))

@@ -63,6 +63,12 @@ bool opts_ok(const sss_walk_opts* o) {
   if (o->unit_paths < 0 || o->regroup < 0 || o->regroup > 32) return false;
   if (o->incidence != 0 && o->incidence != 1) return false;
   if (o->select_pdf != 0 && o->select_pdf != 1) return false;
+  if (o->hero_bands < 0 || o->hero_bands > kHeroMax) return false;
+  if (o->hero_orbits != 0 && o->hero_orbits != 1) return false;
+  if (o->hero_bands > 0 &&
+      (o->hero_texel_bands < o->hero_bands || o->hero_texel_bands % o->hero_bands != 0 ||
+       o->mode != 0))
+    return false;
   if (o->log_r_min_mm < 0.0f || !std::isfinite(o->log_r_min_mm)) return false;
   if (o->log_r_min_mm > 0.0f && (o->log_r_min_mm >= o->r_max_mm || o->nbins < 2)) return false;
   return true;
@@ -146,6 +152,9 @@ WalkConst make_const(const sss_params* p, const sss_walk_opts* o) {
   c.incidence = o->incidence;
   c.entry_fresnel = o->entry_fresnel;
   c.select_uniform = o->select_pdf == 1;
+  c.hero = o->hero_bands;
+  c.hero_nb = o->hero_texel_bands;
+  c.hero_orbits = o->hero_orbits;
   c.log_bins = o->log_r_min_mm > 0.0f;
   c.inv_rmin = c.log_bins ? (float)(1.0 / (double)o->log_r_min_mm) : 0.0f;
   c.inv_log2q = c.log_bins && o->nbins > 1
@@ -206,12 +215,14 @@ sss_status persistent_shape(bool adj, const sss_params* p, const sss_walk_opts* 
   sh->regroup = o->regroup ? o->regroup : 8;
   sh->unit_paths = o->unit_paths ? (uint32_t)o->unit_paths : 1024u;
   // two slots of accumulators per warp; shrink the block for wide histograms
-  const size_t per_warp = (size_t)2 * acc_words * 8 + 2 * kSlotMetaBytes;  // + slot headers
+  // a hero group's slot holds its C members' accumulators
+  const size_t members = o->hero_bands > 0 ? (size_t)o->hero_bands : 1;
+  const size_t per_warp = (size_t)2 * members * acc_words * 8 + 2 * kSlotMetaBytes;
   if (per_warp > kSmemLimit) return SSS_ERR_INVALID_ARG;
   const int max_warps = (int)(kSmemLimit / per_warp);
   if (sh->block / 32 > max_warps) sh->block = max_warps * 32;
   sh->smem = (size_t)(sh->block / 32) * per_warp;
-  const void* fn = persistent_kernel_ptr(adj, p->alpha2 != nullptr);
+  const void* fn = persistent_kernel_ptr(adj, p->alpha2 != nullptr, o->hero_bands);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit) !=
       cudaSuccess)
     return SSS_ERR_CUDA;
@@ -264,7 +275,11 @@ sss_status enqueue_walk(bool adj, const sss_params* p, const sss_walk_opts* o, v
   } else {
     s.prefix = nullptr;
     s.units_per_inst = (p->uniform_paths + (unsigned long long)s.unit_paths - 1) / s.unit_paths;
-    s.total_units = s.units_per_inst * (unsigned long long)p->n_inst;
+    // hero-wavelength sharing schedules groups of hero_bands instances
+    const unsigned long long n_sched =
+        o->hero_bands > 0 ? (unsigned long long)p->n_inst / o->hero_bands
+                          : (unsigned long long)p->n_inst;
+    s.total_units = s.units_per_inst * n_sched;
   }
 
   TallyOut t{};
@@ -325,6 +340,12 @@ sss_status run(bool adj, const sss_params* p, const sss_walk_opts* o, void* ws, 
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1))) return SSS_ERR_INVALID_ARG;
   if (adj && !gout) return SSS_ERR_INVALID_ARG;
   if (adj && p->alpha2) return SSS_ERR_UNSUPPORTED;  // two-layer slabs: forward only
+  if (o->hero_bands > 0) {
+    // hero-wavelength sharing: forward, persistent schedule, one layer,
+    // uniform path budgets, whole texels
+    if (adj || o->schedule != 0 || p->alpha2) return SSS_ERR_UNSUPPORTED;
+    if (p->n_paths || p->n_inst % o->hero_texel_bands != 0) return SSS_ERR_INVALID_ARG;
+  }
   const Layout L = make_layout(p, o, adj);
   if (wsb < L.total) return SSS_ERR_WORKSPACE;
   int sms = 0;

@@ -93,7 +93,12 @@ struct WalkConst {
   int log_bins;
   float inv_rmin, inv_log2q;
   int select_uniform;  // 1: medium chosen uniformly, weight K w_k / sum(w)
+  // hero-wavelength sharing: C bands per group (0 = off), bands per texel,
+  // 1 = rotation orbits {q, q + nb/C, ...}, 0 = blocks of C adjacent bands
+  int hero, hero_nb, hero_orbits;
 };
+
+constexpr int kHeroMax = 4;
 
 enum Event : int { EV_CONTINUE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_DEAD = 3, EV_TRUNC = 4 };
 
@@ -112,6 +117,21 @@ struct Path {
   int layer;
   float gscale, glim, wsum;  // adjoint: fixed-point scale, per-path limit, sum(w)
 };
+
+// Hero-wavelength sharing state of a path of a group of C members: the hero
+// index h and, for the other members m (member (h + 1 + m) mod C), weight W,
+// log2 path-density difference D to the hero, and their optics as alpha,
+// (sigma_h - sigma) log2 e, log2(sigma / sigma_h), g and
+// log2((1 - g^2) / (1 - g_h^2)).  Empty when sharing is off.
+template <int C>
+struct HeroState {
+  int h;
+  float W[C > 1 ? C - 1 : 1], D[C > 1 ? C - 1 : 1];
+  float a[C > 1 ? C - 1 : 1], ds[C > 1 ? C - 1 : 1], ls[C > 1 ? C - 1 : 1],
+      g[C > 1 ? C - 1 : 1], cg[C > 1 ? C - 1 : 1];
+};
+template <>
+struct HeroState<0> {};
 
 // Hardware approximations (one MUFU operation each, a few ulp).
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -190,10 +210,16 @@ __device__ __forceinline__ int select_medium(const WalkConst& c, uint32_t inst, 
   return c.K - 1;
 }
 
-template <bool LAYERED = false>
+// inst indexes the parameter arrays; the random-number counters use
+// instance number inst + instance_offset, or with OWN_CTR = false
+// `ctr_inst` (a hero group's first member).
+template <bool LAYERED = false, bool OWN_CTR = true>
 __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uint32_t path,
-                                          float d, Path& p) {
-  const uint4 r = philox4x32_10_rk(make_uint4(0u, path, inst + c.inst_offset, 1u), c.rk);
+                                          float d, Path& p, uint32_t ctr_inst = 0) {
+  // (the counter instance is spelled out at each use: naming it once costs
+  // the adjoint kernel a register spill)
+  const uint4 r = philox4x32_10_rk(
+      make_uint4(0u, path, OWN_CTR ? inst + c.inst_offset : ctr_inst, 1u), c.rk);
   int k;
   float w_sel = 1.0f;  // w_k / (p_k sum(w)), the estimator weight of the choice
   if (!c.select_uniform) {
@@ -220,7 +246,8 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   if (c.incidence == 1) {
     // cosine-weighted incident lobe: outside cosine sqrt(u), azimuth 2 pi u',
     // refracted by Snell's law; entry weight 1 - F at the refracted angle
-    const uint4 e = philox4x32_10_rk(make_uint4(0u, path, inst + c.inst_offset, 2u), c.rk);
+    const uint4 e = philox4x32_10_rk(
+        make_uint4(0u, path, OWN_CTR ? inst + c.inst_offset : ctr_inst, 2u), c.rk);
     const float mu_o = sqrt_approx(u23(e.x));
     const float sin_i = div_approx(sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu_o, mu_o, 1.0f))),
                                    c.n_rel);
@@ -235,7 +262,7 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.step = 0u;
   p.path = path;
   p.inst = inst;
-  p.cinst = inst + c.inst_offset;
+  p.cinst = OWN_CTR ? inst + c.inst_offset : ctr_inst;
   p.n_coll = 0u;
   p.L = 0.0f;
   p.G = 0.0f;
@@ -246,6 +273,59 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
     p.sigt_o = __ldg(c.sigma_t2 + inst);
     p.fl_o = __fmul_rn(0.693147180559945309f, __fdiv_rn(1.0f, p.sigt_o));
     p.g_o = __ldg(c.g2 + inst);
+  }
+}
+
+// Member j of hero group g: blocks of C adjacent bands of a texel, or the
+// rotation orbits {q, q + nb/C, ...} (Wilkie et al. 2014).
+template <int C>
+__device__ __forceinline__ uint32_t hero_member(const WalkConst& c, uint32_t g, int j) {
+  const uint32_t per = (uint32_t)c.hero_nb / C;  // groups per texel
+  const uint32_t t = g / per, q = g - t * per;
+  return c.hero_orbits ? t * c.hero_nb + q + j * per : t * c.hero_nb + q * C + j;
+}
+
+// Starts path `path` of hero group g: the hero member h = path mod C
+// samples everything (path_init with its optics, under the counters of the
+// group's first member); the other members start with their mixture weight
+// over their selection probability (relative to the hero's) and the log2
+// ratio of their selection probabilities.
+template <int C>
+__device__ __forceinline__ void hero_init(const WalkConst& c, uint32_t g, uint32_t path, float d,
+                                          Path& p, HeroState<C>& hs) {
+  const int h = (int)(path % C);
+  const uint32_t mh = hero_member<C>(c, g, h);
+  path_init<false, false>(c, mh, path, d, p, hero_member<C>(c, g, 0) + c.inst_offset);
+  hs.h = h;
+  p.inst = g;
+  const size_t ok = (size_t)p.k * c.n_inst;
+  const float s_h = p.sigt, g_h = p.g;
+  const float lsh = log2f(s_h), lgh = log2f(__fmaf_rn(-g_h, g_h, 1.0f));
+  // the entry weight before the selection factor, as path_init forms it
+  const float E = c.incidence == 1
+                      ? (c.entry_fresnel ? __fsub_rn(1.0f, fresnel(p.uz, c.n_rel)) : 1.0f)
+                      : c.W0;
+  float tot_h = 0.0f;
+  for (int j = 0; j < c.K; ++j) tot_h = __fadd_rn(tot_h, __ldg(c.w + (size_t)j * c.n_inst + mh));
+  const float lmix_h = log2f(__fdiv_rn(__ldg(c.w + ok + mh), tot_h));
+#pragma unroll
+  for (int m = 0; m < C - 1; ++m) {
+    const uint32_t mj = hero_member<C>(c, g, (h + 1 + m) % C);
+    float tot = 0.0f;
+    for (int j = 0; j < c.K; ++j) tot = __fadd_rn(tot, __ldg(c.w + (size_t)j * c.n_inst + mj));
+    const float wkj = __ldg(c.w + ok + mj);
+    // by w: selection probability = mixture weight, weight E; uniform:
+    // equal selection probabilities, weight E K w_k / sum(w) as path_init
+    hs.W[m] = c.select_uniform
+                  ? __fmul_rn(E, __fmul_rn(__fmul_rn((float)c.K, wkj), __fdiv_rn(1.0f, tot)))
+                  : E;
+    hs.D[m] = c.select_uniform ? 0.0f : __fsub_rn(log2f(__fdiv_rn(wkj, tot)), lmix_h);
+    const float sj = __ldg(c.sigma_t + ok + mj), gj = __ldg(c.g + ok + mj);
+    hs.a[m] = __ldg(c.alpha + ok + mj);
+    hs.ds[m] = __fmul_rn(__fsub_rn(s_h, sj), 1.4426950408889634f);
+    hs.ls[m] = __fsub_rn(log2f(sj), lsh);
+    hs.g[m] = gj;
+    hs.cg[m] = __fsub_rn(log2f(__fmaf_rn(-gj, gj, 1.0f)), lgh);
   }
 }
 
@@ -278,8 +358,8 @@ __device__ __forceinline__ float hg_dlogp_dg(float g, float mu) {
 // collision (weighting, Henyey-Greenstein, rotation) arithmetic and selects
 // the outcome of the event it actually met, so lanes of a warp that meet
 // different events issue the same instructions.
-template <bool ADJ, bool LAYERED = false>
-__device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
+template <bool ADJ, bool LAYERED = false, int HERO = 0>
+__device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<HERO>& hs) {
   if (p.step >= c.max_steps) return EV_TRUNC;
   const uint4 r = philox4x32_10_rk(make_uint4(p.step, p.path, p.cinst, 0u), c.rk);
   p.step++;
@@ -321,9 +401,32 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
   if (c.mode == 0) {
     const float Wn = __fmul_rn(p.W, p.alpha);
     const float An = __fmaf_rn(p.W, __fsub_rn(1.0f, p.alpha), p.Aacc);
-    const bool low = Wn < c.rr_th;
-    dead = !hit && low && !(u3 < __fmul_rn(Wn, c.inv_rr_th));
-    p.W = hit ? p.W : (low ? c.rr_th : Wn);
+    if constexpr (HERO <= 1) {
+      const bool low = Wn < c.rr_th;
+      dead = !hit && low && !(u3 < __fmul_rn(Wn, c.inv_rr_th));
+      p.W = hit ? p.W : (low ? c.rr_th : Wn);
+    } else {
+      // hero-wavelength members: flight density exp(-sigma dist), and on a
+      // collision sigma and the albedo.  Roulette is decided on the largest
+      // member weight Wr and boosts every member by rr_th / Wr.
+      const float coll = hit ? 0.0f : 1.0f;
+      float Wm[HERO > 1 ? HERO - 1 : 1];
+      float Wr = Wn;
+#pragma unroll
+      for (int m = 0; m < HERO - 1; ++m) {
+        hs.D[m] = __fmaf_rn(coll, hs.ls[m], __fmaf_rn(hs.ds[m], dist, hs.D[m]));
+        Wm[m] = __fmul_rn(hs.W[m], hs.a[m]);
+        Wr = fmaxf(Wr, Wm[m]);
+      }
+      const bool low = Wr < c.rr_th;
+      dead = !hit && low && !(u3 < __fmul_rn(Wr, c.inv_rr_th));
+      const float boost = __fmul_rn(c.rr_th, rcp_approx(Wr));
+      p.W = hit ? p.W : (low ? (Wn == Wr ? c.rr_th : __fmul_rn(Wn, boost)) : Wn);
+#pragma unroll
+      for (int m = 0; m < HERO - 1; ++m)
+        hs.W[m] = hit ? hs.W[m]
+                      : (low ? (Wm[m] == Wr ? c.rr_th : __fmul_rn(Wm[m], boost)) : Wm[m]);
+    }
     p.Aacc = hit ? p.Aacc : An;
   } else {
     dead = !hit && (u3 >= p.alpha);
@@ -333,6 +436,18 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p) {
 
   // Henyey-Greenstein scattering with this medium's g.
   const float mu = hg_mu(p.g, u1);
+  if constexpr (HERO > 1) {
+    // log2 p_HG(mu; g_m) - log2 p_HG(mu; g_h)
+    //   = log2((1-g_m^2)/(1-g_h^2)) - 1.5 (log2(1+g_m^2-2 g_m mu) - log2(1+g_h^2-2 g_h mu))
+    const float scat = (hit || dead) ? 0.0f : 1.0f;
+    const float lh = lg2_approx(__fmaf_rn(__fmul_rn(-2.0f, p.g), mu, __fmaf_rn(p.g, p.g, 1.0f)));
+#pragma unroll
+    for (int m = 0; m < HERO - 1; ++m) {
+      const float gm = hs.g[m];
+      const float lm = lg2_approx(__fmaf_rn(__fmul_rn(-2.0f, gm), mu, __fmaf_rn(gm, gm, 1.0f)));
+      hs.D[m] = __fmaf_rn(scat, __fmaf_rn(-1.5f, __fsub_rn(lm, lh), hs.cg[m]), hs.D[m]);
+    }
+  }
   if (ADJ) p.G = (hit || dead) ? p.G : __fadd_rn(p.G, hg_dlogp_dg(p.g, mu));
   // Azimuth phi = 2 pi u2; evaluated as phi - pi in (-pi, pi), then negated.
   float sp, cp;

@@ -272,16 +272,74 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
   if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
 }
 
+// Hero-wavelength exit: every member j of the group scores the one-sample
+// balance-heuristic estimate F_j = W_j C 2^(D_j) / sum_i 2^(D_i), with D the
+// log2 path density relative to the hero (D = 0 for the hero itself).  The
+// slot holds the members' accumulators one after the other (member order).
+template <int C>
+__device__ __forceinline__ void tally_path_hero(const WalkConst& c, const WalkSched& s,
+                                                const TallyOut& t, const Path& p,
+                                                const HeroState<C>& hs, int ev,
+                                                unsigned long long* m, bool direct) {
+  const int nb = c.nbins, sw = s.slot_words;
+  auto add = [&](int j, int w, unsigned long long v) {
+    if (!direct) atomicAdd(m + j * sw + w, v);
+    else atomicAdd(t.raw + (size_t)hero_member<C>(c, p.inst, j) * sw + w, v);
+  };
+  float F[C];
+  if (ev == EV_TOP || ev == EV_BOTTOM) {
+    float dmax = 0.0f;
+#pragma unroll
+    for (int r = 0; r < C - 1; ++r) dmax = fmaxf(dmax, hs.D[r]);
+    float E[C];
+    E[0] = exp2f(-dmax);
+    float S = E[0];
+#pragma unroll
+    for (int r = 0; r < C - 1; ++r) {
+      E[r + 1] = exp2f(__fsub_rn(hs.D[r], dmax));
+      S = __fadd_rn(S, E[r + 1]);
+    }
+    const float scale = __fdiv_rn((float)C, S);
+    F[0] = __fmul_rn(__fmul_rn(p.W, E[0]), scale);
+#pragma unroll
+    for (int r = 0; r < C - 1; ++r) F[r + 1] = __fmul_rn(__fmul_rn(hs.W[r], E[r + 1]), scale);
+  } else {
+#pragma unroll
+    for (int r = 0; r < C; ++r) F[r] = 0.0f;
+  }
+  const int bin = ev == EV_TOP ? exit_bin(c, p) : 0;
+#pragma unroll
+  for (int r = 0; r < C; ++r) {
+    const int j = (hs.h + r) % C;  // r = 0 is the hero
+    if (ev == EV_TOP) {
+      const unsigned long long q = __float2ull_rn(__fmul_rn(F[r], kFix));
+      add(j, bin, q);
+      add(j, nb + 1 + p.k, q);
+      if (p.n_coll == 1u) add(j, nb + 1 + c.K, q);
+      if (s.want_sumsq)
+        add(j, nb + 6 + c.K + bin, __float2ull_rn(__fmul_rn(__fmul_rn(F[r], F[r]), kFix)));
+    } else if (ev == EV_BOTTOM) {
+      add(j, nb + 2 + c.K, __float2ull_rn(__fmul_rn(F[r], kFix)));
+    } else if (ev == EV_TRUNC) {
+      add(j, nb + 4 + c.K, 1ull);
+    }
+    add(j, nb + 5 + c.K, (unsigned long long)p.step);
+  }
+  if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
+}
+
 // The forward one-layer kernel is held to 48 registers: five 256-thread
-// blocks per SM (40 warps) keep the issue slots busy.
-template <bool ADJ, bool LAYERED>
-__global__ void __launch_bounds__(256, (ADJ || LAYERED) ? 4 : 5)
+// blocks per SM (40 warps) keep the issue slots busy.  HERO = C > 0: each
+// scheduled "instance" is a hero group of C bands, and a slot holds the C
+// members' accumulators.
+template <bool ADJ, bool LAYERED, int HERO>
+__global__ void __launch_bounds__(256, HERO >= 4 ? 3 : ((ADJ || LAYERED || HERO) ? 4 : 5))
 walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   extern __shared__ unsigned long long smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int slot_words = s.slot_words;
+  const int slot_words = (HERO > 0 ? HERO : 1) * s.slot_words;
   unsigned long long* slot_mem = smem + (size_t)wib * 2 * slot_words;
   SlotMeta* meta =
       reinterpret_cast<SlotMeta*>(smem + (size_t)nwarps * 2 * slot_words) + 2 * wib;
@@ -301,6 +359,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   int ev = EV_CONTINUE;
   Path p;
   p.step = 0;
+  HeroState<HERO> hs;
 
   // Takes the next unit from the global queue into slot o.
   auto fetch = [&](int o) -> bool {
@@ -326,7 +385,9 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
       sm.next = r.p0;
       sm.end = r.p1;
       sm.live = 1u;
-      sm.d = c.thickness ? __ldg(c.thickness + r.inst) : __int_as_float(0x7f800000);
+      uint32_t dinst = r.inst;
+      if constexpr (HERO > 0) dinst = hero_member<HERO>(c, r.inst, 0);
+      sm.d = c.thickness ? __ldg(c.thickness + dinst) : __int_as_float(0x7f800000);
       sm.scale = scale;
       sm.lim = lim;
       sm.wsum = wsum;
@@ -346,8 +407,15 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     for (int j = lane; j < slot_words; j += 32) {
       const unsigned long long v = m[j];
       if (v != 0ull) {
-        if (ADJ) atomicAdd(t.raw + (size_t)j * c.n_inst + inst, v);  // [4][K][n_inst]
-        else atomicAdd(t.raw + (size_t)inst * slot_words + j, v);
+        if constexpr (ADJ) {
+          atomicAdd(t.raw + (size_t)j * c.n_inst + inst, v);  // [4][K][n_inst]
+        } else if constexpr (HERO > 0) {
+          const int mem = j / s.slot_words;  // member, then its word
+          const uint32_t mi = hero_member<HERO>(c, inst, mem);
+          atomicAdd(t.raw + (size_t)mi * s.slot_words + (j - mem * s.slot_words), v);
+        } else {
+          atomicAdd(t.raw + (size_t)inst * slot_words + j, v);
+        }
         m[j] = 0ull;
       }
     }
@@ -367,8 +435,12 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     if (n_nr >= s.regroup || n_nr == 32) {
       // ---- 1. finished lanes tally together (one divergent block) ----
       if (st == LANE_DONE) {
-        tally_path<ADJ>(c, s, gi, t, p, ev, slot_mem + (size_t)myslot * slot_words,
-                        meta[myslot].gen != mygen);
+        if constexpr (HERO > 0)
+          tally_path_hero<HERO>(c, s, t, p, hs, ev, slot_mem + (size_t)myslot * slot_words,
+                                meta[myslot].gen != mygen);
+        else
+          tally_path<ADJ>(c, s, gi, t, p, ev, slot_mem + (size_t)myslot * slot_words,
+                          meta[myslot].gen != mygen);
         st = LANE_IDLE;
       }
       // ---- 2. refill idle lanes from the current unit (regrouping) ----
@@ -380,7 +452,10 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
           const int rank = __popc(idle & ((1u << lane) - 1u));
           __syncwarp();
           if (st == LANE_IDLE && (uint32_t)rank < take) {
-            path_init<LAYERED>(c, meta[cur].inst, c.path_offset + nxt + rank, meta[cur].d, p);
+            if constexpr (HERO > 0)
+              hero_init<HERO>(c, meta[cur].inst, c.path_offset + nxt + rank, meta[cur].d, p, hs);
+            else
+              path_init<LAYERED>(c, meta[cur].inst, c.path_offset + nxt + rank, meta[cur].d, p);
             if (ADJ) {
               p.gscale = meta[cur].scale;
               p.glim = meta[cur].lim;
@@ -415,7 +490,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     }
     // ---- advance every running path by one draw ----
     if (st == LANE_RUNNING) {
-      ev = path_step<ADJ, LAYERED>(c, p);
+      ev = path_step<ADJ, LAYERED, HERO>(c, p, hs);
       if (ev != EV_CONTINUE) st = LANE_DONE;
     }
   }
@@ -436,11 +511,12 @@ walk_plain_kernel(WalkConst c, WalkSched s, TallyOut t, uint32_t inst, uint32_t 
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < N) {
     Path p;
+    HeroState<0> none;
     const float d = c.thickness ? c.thickness[inst] : __int_as_float(0x7f800000);
     path_init<LAYERED>(c, inst, c.path_offset + j, d, p);
     int ev;
     do {
-      ev = path_step<false, LAYERED>(c, p);
+      ev = path_step<false, LAYERED>(c, p, none);
     } while (ev == EV_CONTINUE);
     const int nb = c.nbins;
     if (ev == EV_TOP) {
@@ -566,15 +642,22 @@ void launch_unit_prefix(const uint32_t* n_paths, uint32_t n, uint32_t C,
 void launch_walk_persistent(bool adj, int grid, int block, size_t smem, const WalkConst& c,
                             const WalkSched& s, const TallyOut& t, const GradIn& gi,
                             cudaStream_t st) {
-  if (adj) walk_persistent_kernel<true, false><<<grid, block, smem, st>>>(c, s, t, gi);
-  else if (c.alpha2) walk_persistent_kernel<false, true><<<grid, block, smem, st>>>(c, s, t, gi);
-  else walk_persistent_kernel<false, false><<<grid, block, smem, st>>>(c, s, t, gi);
+  const void* fn = persistent_kernel_ptr(adj, c.alpha2 != nullptr, c.hero);
+  void* args[] = {const_cast<WalkConst*>(&c), const_cast<WalkSched*>(&s),
+                  const_cast<TallyOut*>(&t), const_cast<GradIn*>(&gi)};
+  cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
-const void* persistent_kernel_ptr(bool adj, bool layered) {
-  return adj ? (const void*)walk_persistent_kernel<true, false>
-             : (layered ? (const void*)walk_persistent_kernel<false, true>
-                        : (const void*)walk_persistent_kernel<false, false>);
+const void* persistent_kernel_ptr(bool adj, bool layered, int hero) {
+  if (adj) return (const void*)walk_persistent_kernel<true, false, 0>;
+  if (layered) return (const void*)walk_persistent_kernel<false, true, 0>;
+  switch (hero) {
+    case 1: return (const void*)walk_persistent_kernel<false, false, 1>;
+    case 2: return (const void*)walk_persistent_kernel<false, false, 2>;
+    case 3: return (const void*)walk_persistent_kernel<false, false, 3>;
+    case 4: return (const void*)walk_persistent_kernel<false, false, 4>;
+    default: return (const void*)walk_persistent_kernel<false, false, 0>;
+  }
 }
 
 void launch_walk_plain(const WalkConst& c, const WalkSched& s, const TallyOut& t, uint32_t inst,

@@ -430,6 +430,25 @@ def test_hero_walk_identical_members_share_every_tally():
     assert abs(h["R"][0] - one["R"][0]) <= Z * np.hypot(h["se_R"][0], one["se_R"][0])
 
 
+def test_hero_walk_uniform_selection_with_zero_weights_is_unbiased():
+    # uniform selection lets a hero pick a medium it gives no weight: the
+    # path must still serve the other members, so roulette is decided on
+    # the largest member weight (a rule on the hero's alone loses them)
+    a = np.array([[0.97] * 3, [0.9] * 3, [0.99] * 3], np.float32)
+    s = np.array([[2.0] * 3, [8.0] * 3, [1.0] * 3], np.float32)
+    g = np.array([[0.8] * 3, [0.3] * 3, [0.6] * 3], np.float32)
+    w = np.array([[1.0, 1.0, 0.0], [0.0, 1.0, 1.0], [1.0, 1.0, 1.0]], np.float32)
+    N = 40000
+    o = oracle.OracleOpts(nbins=8, r_max_mm=4.0, seed=31, select_pdf=1)
+    h = oracle.walk_hero(a, s, g, w, N, 3, 3, None, 1.4, o)
+    sep = oracle.walk(a, s, g, w, np.full(3, N, np.uint32), None, 1.4,
+                      oracle.OracleOpts(nbins=8, r_max_mm=4.0, seed=32))
+    z = (h["R"] - sep["R"]) / np.hypot(h["se_R"], sep["se_R"])
+    assert np.all(np.abs(z) < Z), z
+    zk = (h["R_k"] - sep["R_k"]) / np.maximum(np.hypot(h["se_R_k"], sep["se_R_k"]), 1e-12)
+    assert np.all(np.abs(zk) < Z), zk
+
+
 def test_log_bins_partition_the_same_exits():
     # logarithmic bins (512 to 50 mm, as the paper's generator) regroup the
     # same exits: their sum equals the linear bins' sum plus overflow, and a

@@ -149,6 +149,77 @@ def test_uniform_selection_pdf_parity(api):
     assert np.sqrt(np.mean(z ** 2)) < 1.3
 
 
+def _hero_oracle(x, o, C, orbits):
+    return oracle.walk_hero(x.alpha, x.sigma_t, x.g, x.w, int(x.n_paths[0]), C, 81,
+                            x.thickness_mm, x.n_rel, to_oracle_opts(o), orbits=orbits)
+
+
+def test_hero_wavelength_parity(api):
+    # hero-wavelength sharing (Wilkie et al. 2014): C = 1 is the plain walk
+    # bit for bit (the absorbed tally aside, which hero mode does not score);
+    # C = 3 over adjacent bands and over rotation orbits matches the oracle's
+    # hero walk on the same streams
+    x = inputs.spectral_field(n_texels=2, param_seed=5, n_paths=6000)
+    base = opts(api, nbins=32, r_max_mm=10.0, seed=404)
+    ref, code, flags = run_gpu(x, base, raw=True)
+    assert code == 0
+    one, code, flags = run_gpu(x, opts(api, nbins=32, r_max_mm=10.0, seed=404, hero_bands=1,
+                                       hero_texel_bands=81), raw=True)
+    assert code == 0 and flags == 0
+    K = x.K
+    a_word = 32 + 3 + K
+    keep = [j for j in range(ref["raw"].shape[1]) if j != a_word]
+    np.testing.assert_array_equal(one["raw"][:, keep], ref["raw"][:, keep])
+    assert np.all(one["raw"][:, a_word] == 0)
+    for orbits in (0, 1):
+        o = opts(api, nbins=32, r_max_mm=10.0, seed=405, hero_bands=3, hero_texel_bands=81,
+                 hero_orbits=orbits)
+        g, code, flags = run_gpu(x, o)
+        assert code == 0 and flags == 0
+        r = _hero_oracle(x, o, 3, bool(orbits))
+        worst, where = compare_same_stream(g, r, x.n_paths, r["steps"])
+        print("hero C=3", "orbits" if orbits else "adjacent", "same-stream worst ratio",
+              worst, where)
+        assert worst <= 1.0, where
+
+
+def test_hero_wavelength_is_unbiased_and_shares_paths(api):
+    # one shared path per group of 3 adjacent bands against one path per
+    # band: the same tallies within the statistical bar, about the same
+    # standard error, a third of the paths
+    x = inputs.spectral_field(n_texels=8, param_seed=6, n_paths=1 << 15)
+    g, code, _ = run_gpu(x, opts(api, nbins=32, r_max_mm=10.0, seed=7, hero_bands=3,
+                                 hero_texel_bands=81))
+    assert code == 0
+    s, _, _ = run_gpu(x, opts(api, nbins=32, r_max_mm=10.0, seed=8))
+    z = (g["R"] - s["R"]) / np.hypot(g["stderr_R"], s["stderr_R"])
+    print("hero vs per-band R: z rms", np.sqrt(np.mean(z ** 2)), "max", np.abs(z).max(),
+          "se ratio median", np.median(g["stderr_R"] / s["stderr_R"]))
+    assert np.sqrt(np.mean(z ** 2)) < 1.2 and np.abs(z).max() < 5.0
+    assert np.median(g["stderr_R"] / s["stderr_R"]) < 1.1
+
+
+def test_hero_wavelength_argument_checks(api):
+    import torch
+    x = inputs.spectral_field(n_texels=1, param_seed=5, n_paths=1000)
+    m = api.Media.from_inputs(x)
+    bad = [dict(hero_bands=5, hero_texel_bands=81), dict(hero_bands=2, hero_texel_bands=81),
+           dict(hero_bands=3, hero_texel_bands=80), dict(hero_bands=3, hero_texel_bands=81,
+                                                         mode=1)]
+    for kw in bad:
+        with pytest.raises(api.SSSError) as e:
+            api.walk(m, opts(api, **kw))
+        assert e.value.code == 1, kw
+    mp = api.Media.from_inputs(x, per_instance_paths=True)
+    with pytest.raises(api.SSSError) as e:
+        api.walk(mp, opts(api, hero_bands=3, hero_texel_bands=81))
+    assert e.value.code == 1
+    with pytest.raises(api.SSSError) as e:
+        api.walk(m, opts(api, hero_bands=3, hero_texel_bands=81, schedule=1))
+    assert e.value.code == 7
+    torch.cuda.synchronize()
+
+
 def test_two_layer_slab_parity_and_limits(api):
     # skin-like two-layer slabs: same-stream parity with the oracle, the
     # plain baseline bit-identical, and a top layer too thick to cross
