@@ -537,6 +537,8 @@ def main():
         hts = []
         for _ in range(2):
             ha, hb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ha.record(stream)   # creates the CUDA events
+            hb.record(stream)
             api.profile_events(ha, hb)
             api.walk(m, oh, workspace=wh, out=th_)
             api.profile_events(None, None)

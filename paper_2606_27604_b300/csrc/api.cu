@@ -27,6 +27,7 @@ struct Layout {
   size_t header = 0;       // status u32 @0, unit counter u64 @8, total units u64 @16
   size_t block_sums = 0;   // uneven budgets: per-256-instance unit sums
   size_t prefix = 0;       // uneven budgets: [n_inst+1] unit prefix
+  size_t hero = 0;         // hero-wavelength sharing: [3][K][n_inst] float log table
   size_t acc = 0;          // fixed-point accumulators
   size_t total = 0;
   int acc_words = 0;       // per instance (forward) or per slot (adjoint)
@@ -85,6 +86,10 @@ Layout make_layout(const sss_params* p, const sss_walk_opts* o, bool adj) {
     off += align_up(((n + 255) / 256 + 1) * 8);
     L.prefix = off;
     off += align_up((n + 1) * 8);
+  }
+  if (!adj && o->hero_bands > 0) {
+    L.hero = off;
+    off += align_up((size_t)3 * p->K * n * 4);
   }
   L.acc = off;
   if (adj) {
@@ -155,6 +160,7 @@ WalkConst make_const(const sss_params* p, const sss_walk_opts* o) {
   c.hero = o->hero_bands;
   c.hero_nb = o->hero_texel_bands;
   c.hero_orbits = o->hero_orbits;
+  c.hero_logs = nullptr;  // set by enqueue_walk (workspace)
   c.log_bins = o->log_r_min_mm > 0.0f;
   c.inv_rmin = c.log_bins ? (float)(1.0 / (double)o->log_r_min_mm) : 0.0f;
   c.inv_log2q = c.log_bins && o->nbins > 1
@@ -244,13 +250,15 @@ sss_status enqueue_walk(bool adj, const sss_params* p, const sss_walk_opts* o, v
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(base + L.header + 8);
   unsigned long long* total = reinterpret_cast<unsigned long long*>(base + L.header + 16);
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(base + L.acc);
-  const WalkConst c = make_const(p, o);
+  WalkConst c = make_const(p, o);
+  if (c.hero > 0) c.hero_logs = reinterpret_cast<const float*>(base + L.hero);
 
   // zero the header and the accumulators
   if (cudaMemsetAsync(base + L.header, 0, kAlign, st) != cudaSuccess) return SSS_ERR_CUDA;
   if (L.total > L.acc && cudaMemsetAsync(acc, 0, L.total - L.acc, st) != cudaSuccess)
     return SSS_ERR_CUDA;
   launch_validate(c, status, st);
+  if (c.hero > 0) launch_hero_logs(c, reinterpret_cast<float*>(base + L.hero), st);
 
   Shape sh{};
   if (o->schedule == 0 || adj) {

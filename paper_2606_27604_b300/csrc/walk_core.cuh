@@ -96,6 +96,7 @@ struct WalkConst {
   // hero-wavelength sharing: C bands per group (0 = off), bands per texel,
   // 1 = rotation orbits {q, q + nb/C, ...}, 0 = blocks of C adjacent bands
   int hero, hero_nb, hero_orbits;
+  const float* hero_logs;  // [3][K][n_inst]: log2 sigma_t, log2(1 - g^2), log2 mixture weight
 };
 
 constexpr int kHeroMax = 4;
@@ -273,59 +274,6 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
     p.sigt_o = __ldg(c.sigma_t2 + inst);
     p.fl_o = __fmul_rn(0.693147180559945309f, __fdiv_rn(1.0f, p.sigt_o));
     p.g_o = __ldg(c.g2 + inst);
-  }
-}
-
-// Member j of hero group g: blocks of C adjacent bands of a texel, or the
-// rotation orbits {q, q + nb/C, ...} (Wilkie et al. 2014).
-template <int C>
-__device__ __forceinline__ uint32_t hero_member(const WalkConst& c, uint32_t g, int j) {
-  const uint32_t per = (uint32_t)c.hero_nb / C;  // groups per texel
-  const uint32_t t = g / per, q = g - t * per;
-  return c.hero_orbits ? t * c.hero_nb + q + j * per : t * c.hero_nb + q * C + j;
-}
-
-// Starts path `path` of hero group g: the hero member h = path mod C
-// samples everything (path_init with its optics, under the counters of the
-// group's first member); the other members start with their mixture weight
-// over their selection probability (relative to the hero's) and the log2
-// ratio of their selection probabilities.
-template <int C>
-__device__ __forceinline__ void hero_init(const WalkConst& c, uint32_t g, uint32_t path, float d,
-                                          Path& p, HeroState<C>& hs) {
-  const int h = (int)(path % C);
-  const uint32_t mh = hero_member<C>(c, g, h);
-  path_init<false, false>(c, mh, path, d, p, hero_member<C>(c, g, 0) + c.inst_offset);
-  hs.h = h;
-  p.inst = g;
-  const size_t ok = (size_t)p.k * c.n_inst;
-  const float s_h = p.sigt, g_h = p.g;
-  const float lsh = log2f(s_h), lgh = log2f(__fmaf_rn(-g_h, g_h, 1.0f));
-  // the entry weight before the selection factor, as path_init forms it
-  const float E = c.incidence == 1
-                      ? (c.entry_fresnel ? __fsub_rn(1.0f, fresnel(p.uz, c.n_rel)) : 1.0f)
-                      : c.W0;
-  float tot_h = 0.0f;
-  for (int j = 0; j < c.K; ++j) tot_h = __fadd_rn(tot_h, __ldg(c.w + (size_t)j * c.n_inst + mh));
-  const float lmix_h = log2f(__fdiv_rn(__ldg(c.w + ok + mh), tot_h));
-#pragma unroll
-  for (int m = 0; m < C - 1; ++m) {
-    const uint32_t mj = hero_member<C>(c, g, (h + 1 + m) % C);
-    float tot = 0.0f;
-    for (int j = 0; j < c.K; ++j) tot = __fadd_rn(tot, __ldg(c.w + (size_t)j * c.n_inst + mj));
-    const float wkj = __ldg(c.w + ok + mj);
-    // by w: selection probability = mixture weight, weight E; uniform:
-    // equal selection probabilities, weight E K w_k / sum(w) as path_init
-    hs.W[m] = c.select_uniform
-                  ? __fmul_rn(E, __fmul_rn(__fmul_rn((float)c.K, wkj), __fdiv_rn(1.0f, tot)))
-                  : E;
-    hs.D[m] = c.select_uniform ? 0.0f : __fsub_rn(log2f(__fdiv_rn(wkj, tot)), lmix_h);
-    const float sj = __ldg(c.sigma_t + ok + mj), gj = __ldg(c.g + ok + mj);
-    hs.a[m] = __ldg(c.alpha + ok + mj);
-    hs.ds[m] = __fmul_rn(__fsub_rn(s_h, sj), 1.4426950408889634f);
-    hs.ls[m] = __fsub_rn(log2f(sj), lsh);
-    hs.g[m] = gj;
-    hs.cg[m] = __fsub_rn(log2f(__fmaf_rn(-gj, gj, 1.0f)), lgh);
   }
 }
 

@@ -20,16 +20,17 @@
 //                       upstream derivatives instead of tallies.
 //   walk_plain        : baseline: one thread per path of one instance.
 //   finalize_*        : fixed point -> float64 means / standard errors.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "walk_core.cuh"
 #include "walk_kernels.cuh"
 
+#include "hero.cuh"
+
 namespace sss {
 
-static constexpr float kFix = 4294967296.0f;  // 2^32
-static constexpr double kInvFix = 1.0 / 4294967296.0;
 static constexpr unsigned kFull = 0xffffffffu;
 
 // -------------------------------------------------------------- validate --
@@ -272,62 +273,6 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
   if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
 }
 
-// Hero-wavelength exit: every member j of the group scores the one-sample
-// balance-heuristic estimate F_j = W_j C 2^(D_j) / sum_i 2^(D_i), with D the
-// log2 path density relative to the hero (D = 0 for the hero itself).  The
-// slot holds the members' accumulators one after the other (member order).
-template <int C>
-__device__ __forceinline__ void tally_path_hero(const WalkConst& c, const WalkSched& s,
-                                                const TallyOut& t, const Path& p,
-                                                const HeroState<C>& hs, int ev,
-                                                unsigned long long* m, bool direct) {
-  const int nb = c.nbins, sw = s.slot_words;
-  auto add = [&](int j, int w, unsigned long long v) {
-    if (!direct) atomicAdd(m + j * sw + w, v);
-    else atomicAdd(t.raw + (size_t)hero_member<C>(c, p.inst, j) * sw + w, v);
-  };
-  float F[C];
-  if (ev == EV_TOP || ev == EV_BOTTOM) {
-    float dmax = 0.0f;
-#pragma unroll
-    for (int r = 0; r < C - 1; ++r) dmax = fmaxf(dmax, hs.D[r]);
-    float E[C];
-    E[0] = exp2f(-dmax);
-    float S = E[0];
-#pragma unroll
-    for (int r = 0; r < C - 1; ++r) {
-      E[r + 1] = exp2f(__fsub_rn(hs.D[r], dmax));
-      S = __fadd_rn(S, E[r + 1]);
-    }
-    const float scale = __fdiv_rn((float)C, S);
-    F[0] = __fmul_rn(__fmul_rn(p.W, E[0]), scale);
-#pragma unroll
-    for (int r = 0; r < C - 1; ++r) F[r + 1] = __fmul_rn(__fmul_rn(hs.W[r], E[r + 1]), scale);
-  } else {
-#pragma unroll
-    for (int r = 0; r < C; ++r) F[r] = 0.0f;
-  }
-  const int bin = ev == EV_TOP ? exit_bin(c, p) : 0;
-#pragma unroll
-  for (int r = 0; r < C; ++r) {
-    const int j = (hs.h + r) % C;  // r = 0 is the hero
-    if (ev == EV_TOP) {
-      const unsigned long long q = __float2ull_rn(__fmul_rn(F[r], kFix));
-      add(j, bin, q);
-      add(j, nb + 1 + p.k, q);
-      if (p.n_coll == 1u) add(j, nb + 1 + c.K, q);
-      if (s.want_sumsq)
-        add(j, nb + 6 + c.K + bin, __float2ull_rn(__fmul_rn(__fmul_rn(F[r], F[r]), kFix)));
-    } else if (ev == EV_BOTTOM) {
-      add(j, nb + 2 + c.K, __float2ull_rn(__fmul_rn(F[r], kFix)));
-    } else if (ev == EV_TRUNC) {
-      add(j, nb + 4 + c.K, 1ull);
-    }
-    add(j, nb + 5 + c.K, (unsigned long long)p.step);
-  }
-  if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
-}
-
 // The forward one-layer kernel is held to 48 registers: five 256-thread
 // blocks per SM (40 warps) keep the issue slots busy.  HERO = C > 0: each
 // scheduled "instance" is a hero group of C bands, and a slot holds the C
@@ -386,7 +331,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
       sm.end = r.p1;
       sm.live = 1u;
       uint32_t dinst = r.inst;
-      if constexpr (HERO > 0) dinst = hero_member<HERO>(c, r.inst, 0);
+      if constexpr (HERO > 0) dinst = hero_group<HERO>(c, r.inst).first;
       sm.d = c.thickness ? __ldg(c.thickness + dinst) : __int_as_float(0x7f800000);
       sm.scale = scale;
       sm.lim = lim;
@@ -411,7 +356,8 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
           atomicAdd(t.raw + (size_t)j * c.n_inst + inst, v);  // [4][K][n_inst]
         } else if constexpr (HERO > 0) {
           const int mem = j / s.slot_words;  // member, then its word
-          const uint32_t mi = hero_member<HERO>(c, inst, mem);
+          const HeroGroup G = hero_group<HERO>(c, inst);
+          const uint32_t mi = G.first + (uint32_t)mem * G.stride;
           atomicAdd(t.raw + (size_t)mi * s.slot_words + (j - mem * s.slot_words), v);
         } else {
           atomicAdd(t.raw + (size_t)inst * slot_words + j, v);
@@ -624,6 +570,14 @@ __global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, int
 }
 
 // ---------------------------------------------------------------- launch --
+void launch_hero_logs(const WalkConst& c, float* logs, cudaStream_t st) {
+  const size_t Kn = (size_t)c.K * c.n_inst;
+  if (Kn == 0) return;
+  const int block = 256;
+  const int grid = (int)std::min<size_t>((Kn + block - 1) / block, 148 * 16);
+  hero_logs_kernel<<<grid, block, 0, st>>>(c, logs);
+}
+
 void launch_validate(const WalkConst& c, unsigned int* status, cudaStream_t st) {
   if (c.n_inst == 0) return;
   validate_params_kernel<<<(c.n_inst + 255) / 256, 256, 0, st>>>(c, status);

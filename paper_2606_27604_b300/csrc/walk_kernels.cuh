@@ -16,6 +16,11 @@ enum : unsigned int {
   SSS_DEV_FLAG_ZERO_WEIGHT = 0x8u,
 };
 
+// Tallies are fixed point: an exit weight W adds round(W 2^32) to a uint64
+// word, so sums do not depend on the order of the atomics.
+constexpr float kFix = 4294967296.0f;  // 2^32
+constexpr double kInvFix = 1.0 / 4294967296.0;
+
 // Bytes of the per-slot header (SlotMeta) after a warp's two slots of
 // shared accumulators.
 constexpr int kSlotMetaBytes = 48;
@@ -49,6 +54,8 @@ struct GradOut {
 };
 
 void launch_validate(const WalkConst& c, unsigned int* status, cudaStream_t st);
+// Fills the [3][K][n_inst] log table of hero-wavelength sharing (c.hero > 0).
+void launch_hero_logs(const WalkConst& c, float* logs, cudaStream_t st);
 void launch_unit_prefix(const uint32_t* n_paths, uint32_t n, uint32_t C,
                         unsigned long long* block_sums, unsigned long long* total,
                         unsigned long long* prefix, cudaStream_t st);
