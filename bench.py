@@ -48,8 +48,8 @@ DECODER_MACS_PER_TEXEL = (3 * 256 + 256 * 256 + 256 * 5) + (5 * 512 + 512 * 512 
 # dram__bytes_write.sum) of the 1024-texel case, scaled by 64 to the
 # 65536-texel launch (the traffic grows with the instances walked).  Valid
 # only while the kernel sources are the ones captured (sha1 below).
-WALK_TRAFFIC = {"bytes_per_launch": (61.613568e6 + 11.548160e6) * 64,
-                "source_sha1": "b4920cc88ee3060dceb629c72b7d8960a2b44d21",
+WALK_TRAFFIC = {"bytes_per_launch": (61.705216e6 + 11.656704e6) * 64,
+                "source_sha1": "679dd22c00a894eb1527185534349f180863cabd",
                 "capture": "profiles/walk_persistent_spectral_field.md"}
 
 
