@@ -419,6 +419,30 @@ void sss_release_plans(void);
 /* Static text for a status code. */
 const char* sss_status_string(sss_status s);
 
+/* ------------------------------------------------------------------------ */
+/* Issue-rate probes (no counterpart in the paper: measurement of the        */
+/* per-SM arithmetic throughput that bounds the walk, for its roofline).     */
+/* ------------------------------------------------------------------------ */
+enum {
+  SSS_PROBE_FFMA = 0,   /* binary32 fused multiply-add                        */
+  SSS_PROBE_FFMA2 = 1,  /* paired binary32 fused multiply-add (two lanes' ops) */
+  SSS_PROBE_IMAD = 2,   /* 32-bit integer multiply-add                        */
+  SSS_PROBE_LOP3 = 3,   /* 32-bit three-input logic operation                 */
+  SSS_PROBE_MUFU = 4    /* special-function unit (lg2.approx)                 */
+};
+
+/* Launches `blocks` blocks of 256 threads on `stream`, each thread running
+ * `iters` iterations of eight independent chains of the probed operation,
+ * and writes one float per thread to sink[blocks * 256] (device, caller
+ * owned) so nothing is optimised away.  Asynchronous: time it with events
+ * on the stream.  Operations executed = blocks * 256 * iters *
+ * sss_probe_ops_per_thread_iter(kind).  Errors: SSS_ERR_INVALID_ARG for a
+ * bad kind, iters < 1, blocks < 1 or a null sink; SSS_ERR_CUDA if the
+ * launch fails. */
+sss_status sss_probe(int32_t kind, int64_t iters, int32_t blocks, float* sink,
+                     sss_stream_t stream);
+int64_t sss_probe_ops_per_thread_iter(int32_t kind);
+
 /* SSS_ABI_VERSION of the loaded library. */
 int32_t sss_abi_version(void);
 

@@ -90,6 +90,10 @@ def _load():
     lib.sss_release_plans.restype = None
     lib.sss_status_string.argtypes = [C.c_int]
     lib.sss_status_string.restype = C.c_char_p
+    lib.sss_probe.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
+    lib.sss_probe.restype = C.c_int
+    lib.sss_probe_ops_per_thread_iter.argtypes = [C.c_int32]
+    lib.sss_probe_ops_per_thread_iter.restype = C.c_int64
     lib.sss_abi_version.argtypes = []
     lib.sss_abi_version.restype = C.c_int32
     if lib.sss_abi_version() != ABI_VERSION:
@@ -462,3 +466,15 @@ def lut_fit(R_lut, p_lut, a0, da, g0, dg, drho, r_mm, P_mc, R_mc, raw, K=3, step
                            C.byref(o), _ptr(raw), _ptr(loss), _ptr(grad), _stream(stream)),
            "sss_lut_fit")
     return loss, grad
+
+
+PROBE_KINDS = {"ffma": 0, "ffma2": 1, "imad": 2, "lop3": 3, "mufu_lg2": 4}
+
+
+def probe(kind: str, iters: int, blocks: int, sink: torch.Tensor, stream=None) -> int:
+    """Launches the issue-rate probe `kind` (see sss_probe); returns the lane
+    operations it executes.  `sink` is a float32 CUDA tensor of blocks * 256."""
+    k = PROBE_KINDS[kind]
+    assert sink.is_cuda and sink.dtype == torch.float32 and sink.numel() >= blocks * 256
+    _check(lib.sss_probe(k, iters, blocks, _ptr(sink), _stream(stream)), "sss_probe")
+    return blocks * 256 * iters * lib.sss_probe_ops_per_thread_iter(k)

@@ -7,7 +7,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsss.so")
-SOURCES = ["api.cu", "walk_kernels.cu", "decode.cu", "decode_api.cu", "noalloc.cu", "fit.cu"]
+SOURCES = ["api.cu", "walk_kernels.cu", "decode.cu", "decode_api.cu", "noalloc.cu", "fit.cu",
+           "probe.cu"]
 HEADERS = ["walk_core.cuh", "walk_kernels.cuh", "decode_kernels.cuh", "fit_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
