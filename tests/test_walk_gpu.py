@@ -199,6 +199,31 @@ def test_hero_wavelength_is_unbiased_and_shares_paths(api):
     assert np.median(g["stderr_R"] / s["stderr_R"]) < 1.1
 
 
+def test_hero_wavelength_shards_and_options(api):
+    # texel shards walked with instance_offset reproduce the whole batch bit
+    # for bit; with logarithmic bins, the cosine lobe and uniform selection
+    # the hero walk still matches the oracle's on the same streams
+    x = inputs.spectral_field(n_texels=4, param_seed=11, n_paths=3000)
+    o = opts(api, nbins=24, r_max_mm=8.0, seed=606, hero_bands=3, hero_texel_bands=81)
+    whole, code, _ = run_gpu(x, o, raw=True)
+    assert code == 0
+    for lo, hi in ((0, 1), (1, 4)):
+        part = x.subset(np.arange(lo * 81, hi * 81))
+        got, code, _ = run_gpu(part, opts(api, nbins=24, r_max_mm=8.0, seed=606, hero_bands=3,
+                                          hero_texel_bands=81, instance_offset=lo * 81),
+                               raw=True)
+        assert code == 0
+        np.testing.assert_array_equal(got["raw"], whole["raw"][lo * 81:hi * 81])
+    o2 = opts(api, nbins=48, r_max_mm=20.0, seed=607, hero_bands=3, hero_texel_bands=81,
+              log_r_min_mm=0.02, incidence=1, select_pdf=1)
+    g, code, flags = run_gpu(x, o2)
+    assert code == 0 and flags == 0
+    r = _hero_oracle(x, o2, 3, False)
+    worst, where = compare_same_stream(g, r, x.n_paths, r["steps"])
+    print("hero with options same-stream worst ratio", worst, where)
+    assert worst <= 1.0, where
+
+
 def test_hero_wavelength_argument_checks(api):
     import torch
     x = inputs.spectral_field(n_texels=1, param_seed=5, n_paths=1000)
