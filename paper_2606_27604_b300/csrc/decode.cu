@@ -76,6 +76,39 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// The same copy multicast to every CTA of the cluster in `mask`: the box
+// lands at the same shared-memory offset in each, and each destination's
+// mbarrier at the same offset receives the bytes.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y,
+                                               uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// All threads of all CTAs of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -115,6 +148,16 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
+      : "memory");
+}
+
+// Arrives on the mbarrier at this offset in every CTA of `mask` once the
+// MMAs issued so far have completed.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster"
+      ".b64 [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
       : "memory");
 }
 
@@ -253,10 +296,17 @@ __device__ __forceinline__ void epi_final_group(const float* v, int row, int P,
 // other accumulator (two warps per TMEM lane quarter, alternate 16-column
 // chunks), so a tile's epilogue overlaps the next tile's MMAs.  The bias
 // vector is staged once in shared memory.
+//
+// CM > 1: thread-block clusters of CM CTAs along M share the weight tile.
+// The CTAs of a cluster work on CM consecutive M tiles of the same N tile in
+// step; each loads 1/CM of every B k-block and multicasts it to all of
+// them, so B leaves L2 once per cluster instead of once per CTA.  A stage
+// is refilled only after every CTA's MMAs have read it: each MMA warp's
+// commit arrives on that stage's "empty" barrier in all CTAs (count CM).
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 
-template <int BN, int EPI>
+template <int BN, int EPI, int CM>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                  const __grid_constant__ CUtensorMap tmap_b, int a_x0, int num_kb,
@@ -266,8 +316,13 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
   constexpr int B_BYTES = BN * BK * 2;
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   constexpr int TCOLS = TmemCols<2 * BN>::value2;
+  constexpr int SLICE_ROWS = BN / CM;            // B rows each CTA of a cluster loads
+  constexpr int SLICE_BYTES = SLICE_ROWS * BK * 2;
+  constexpr uint16_t kMask = (uint16_t)((1u << CM) - 1u);
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
   static_assert(B_BYTES % 1024 == 0, "tiles must stay 1024-byte aligned");
+  static_assert(CM >= 1 && CM <= 8 && BN % CM == 0 && SLICE_BYTES % 1024 == 0,
+                "B slices must keep the 1024-byte swizzle atoms whole");
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -282,12 +337,16 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const long long total = m_tiles * (long long)n_tiles;
+  // tiles of the cluster: CM consecutive M tiles x one N tile
+  const int crank = CM > 1 ? (int)cluster_ctarank() : 0;
+  const long long first = CM > 1 ? (long long)cluster_id_x() : (long long)blockIdx.x;
+  const long long step = CM > 1 ? (long long)cluster_count_x() : (long long)gridDim.x;
+  const long long total = ((m_tiles + CM - 1) / CM) * (long long)n_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CM);  // one commit from each CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -307,6 +366,7 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
   for (int j = threadIdx.x; j < n_tiles * BN; j += blockDim.x) sbias[j] = bias[j];
   tc_fence_before();
   __syncthreads();
+  if (CM > 1) cluster_sync();  // every CTA's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -317,8 +377,8 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap_b))
                    : "memory");
       long long it = 0;
-      for (long long t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
-        const int m_tile = (int)(t / n_tiles), n_tile = (int)(t % n_tiles);
+      for (long long t = first; t < total && !*abort_flag; t += step) {
+        const int m_tile = (int)((t / n_tiles) * CM + crank), n_tile = (int)(t % n_tiles);
         for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = (int)(it % STAGES);
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -327,10 +387,14 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
             *abort_flag = 1u;
             break;
           }
-          mbar_expect_tx(&full[s], STAGE_BYTES);
+          mbar_expect_tx(&full[s], STAGE_BYTES);  // own A + every slice of B
           uint8_t* sa = smem + s * STAGE_BYTES;
           tma_load_2d(sa, &tmap_a, a_x0 + kb * BK, m_tile * BM, &full[s]);
-          tma_load_2d(sa + A_BYTES, &tmap_b, kb * BK, n_tile * BN, &full[s]);
+          if (CM == 1)
+            tma_load_2d(sa + A_BYTES, &tmap_b, kb * BK, n_tile * BN, &full[s]);
+          else
+            tma_load_2d_mc(sa + A_BYTES + crank * SLICE_BYTES, &tmap_b, kb * BK,
+                           n_tile * BN + crank * SLICE_ROWS, &full[s], kMask);
         }
       }
     }
@@ -339,7 +403,7 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
       constexpr uint32_t idesc = idesc_bf16<BN>();
       long long it = 0;
       int i = 0;
-      for (long long t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++i) {
+      for (long long t = first; t < total && !*abort_flag; t += step, ++i) {
         const int b = i & 1;
         if (!mbar_wait(&tempty[b], ((uint32_t)(i >> 1) & 1u) ^ 1u)) {
           atomicOr(status, DEC_FLAG_TIMEOUT);
@@ -362,7 +426,9 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)  // K = 16 per MMA: advance 32 bytes
             umma_bf16(acc, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
-          umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+          // frees the stage (in every CTA of the cluster) once these MMAs have read it
+          if (CM == 1) umma_commit(&empty[s]);
+          else umma_commit_mc(&empty[s], kMask);
         }
         umma_commit(&tfull[b]);    // accumulator b complete
       }
@@ -372,8 +438,8 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
     const int q = warp & 3;          // TMEM lane quarter this warp may read
     const int half = (warp - 2) >> 2;  // which alternate column chunks
     int i = 0;
-    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-      const int m_tile = (int)(t / n_tiles), n_tile = (int)(t % n_tiles);
+    for (long long t = first; t < total; t += step, ++i) {
+      const int m_tile = (int)((t / n_tiles) * CM + crank), n_tile = (int)(t % n_tiles);
       const int b = i & 1;
       const bool ok = mbar_wait(&tfull[b], (uint32_t)(i >> 1) & 1u);
       if (!ok) {
@@ -425,6 +491,8 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
   }
   tc_fence_before();
   __syncthreads();
+  // no CTA leaves while another may still signal its barriers
+  if (CM > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -488,7 +556,7 @@ __global__ void pack_weights_kernel(const __nv_bfloat16* __restrict__ src, int s
 }
 
 // ---------------------------------------------------------------- launch --
-template <int BN, int EPI>
+template <int BN, int EPI, int CM>
 static cudaError_t launch_gemm_t(const CUtensorMap& ta, const CUtensorMap& tb, int a_x0,
                                  int num_kb, int n_tiles, long long m_tiles, const float* bias,
                                  const EpiParams& ep, unsigned int* status, cudaStream_t st) {
@@ -497,31 +565,61 @@ static cudaError_t launch_gemm_t(const CUtensorMap& ta, const CUtensorMap& tb, i
   constexpr size_t ring = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2);
   const size_t smem = (ring > 120 * 1024 ? ring : 120 * 1024) + 1024 + 256 +
                       (size_t)n_tiles * BN * sizeof(float);
-  auto fn = gemm_bf16_kernel<BN, EPI>;
+  auto fn = gemm_bf16_kernel<BN, EPI, CM>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long total = (long long)n_tiles * m_tiles;
-  const unsigned grid = (unsigned)(total < sms ? total : sms);
-  if (grid == 0) return cudaSuccess;
-  fn<<<grid, kThreads, smem, st>>>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status);
-  return cudaGetLastError();
+  const long long total = (long long)n_tiles * ((m_tiles + CM - 1) / CM);  // cluster tiles
+  if (total == 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  long long slots = sms;  // resident CTAs
+  if (CM > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CM;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(sms / CM * CM));
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    slots = (long long)clusters * CM;
+  }
+  const long long ctas = (total < slots / CM ? total : slots / CM) * CM;
+  cfg.gridDim = dim3((unsigned)ctas);
+  return cudaLaunchKernelEx(&cfg, fn, ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status);
 }
 
-cudaError_t launch_gemm(int bn, int epi, const CUtensorMap& ta, const CUtensorMap& tb, int a_x0,
-                        int num_kb, int n_tiles, long long m_tiles, const float* bias,
+cudaError_t launch_gemm(int bn, int epi, int cm, const CUtensorMap& ta, const CUtensorMap& tb,
+                        int a_x0, int num_kb, int n_tiles, long long m_tiles, const float* bias,
                         const EpiParams& ep, unsigned int* status, cudaStream_t st) {
-  if (epi == EPI_FINAL && bn == 144)
-    return launch_gemm_t<144, EPI_FINAL>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st);
+#define SSS_GEMM(BN_, EPI_, CM_) \
+  return launch_gemm_t<BN_, EPI_, CM_>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st)
+  if (epi == EPI_FINAL && bn == 144) {
+    if (cm == 2) SSS_GEMM(144, EPI_FINAL, 2);
+    SSS_GEMM(144, EPI_FINAL, 1);
+  }
   if (epi == EPI_HIDDEN) {
     switch (bn) {
-      case 16: return launch_gemm_t<16, EPI_HIDDEN>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st);
-      case 128: return launch_gemm_t<128, EPI_HIDDEN>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st);
-      case 256: return launch_gemm_t<256, EPI_HIDDEN>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st);
+      case 16: SSS_GEMM(16, EPI_HIDDEN, 1);
+      case 128:
+        if (cm == 2) SSS_GEMM(128, EPI_HIDDEN, 2);
+        SSS_GEMM(128, EPI_HIDDEN, 1);
+      case 256:
+        if (cm == 4) SSS_GEMM(256, EPI_HIDDEN, 4);
+        if (cm == 2) SSS_GEMM(256, EPI_HIDDEN, 2);
+        SSS_GEMM(256, EPI_HIDDEN, 1);
     }
   }
+#undef SSS_GEMM
   return cudaErrorInvalidValue;
 }
 
