@@ -147,9 +147,32 @@ def cpu_baseline_sample(n_texels=24):
     oracle.walk(x.alpha, x.sigma_t, x.g, x.w, x.n_paths, None, x.n_rel, o)
     dt = time.perf_counter() - t0
     paths = int(x.n_paths.sum())
+    # the other configurations' shapes, each a bounded sample
+    per_config = {}
+    x0 = inputs.single_wavelength(param_seed=0, n_paths=1 << 18)
+    o0 = oracle.OracleOpts(nbins=32, r_max_mm=10.0, seed=1000)
+    t = time.perf_counter()
+    r0 = oracle.walk(x0.alpha, x0.sigma_t, x0.g, x0.w, x0.n_paths, None, x0.n_rel, o0)
+    d0 = time.perf_counter() - t
+    p0 = int(x0.n_paths.sum())
+    per_config["single_wavelength_16_sets"] = {
+        "paths_per_s": p0 / d0, "sample": f"all 16 sets x 2^18 paths ({p0} paths), {d0:.1f} s",
+        "steps_per_path": float(np.mean(r0["steps"]))}
+    xu = inputs.uneven_batch(n_inst=4096, param_seed=2).subset(np.arange(0, 4096, 64))
+    ou = oracle.OracleOpts(nbins=64, r_max_mm=10.0, seed=1002)
+    t = time.perf_counter()
+    ru = oracle.walk(xu.alpha, xu.sigma_t, xu.g, xu.w, xu.n_paths, xu.thickness_mm, xu.n_rel, ou)
+    du = time.perf_counter() - t
+    pu = int(xu.n_paths.astype(np.int64).sum())
+    per_config["uneven_batch"] = {
+        "paths_per_s": pu / du,
+        "sample": f"every 64th of the 4096 uneven instances ({xu.n_inst} instances, {pu} paths), "
+                  f"{du:.1f} s",
+        "steps_per_path": float(np.average(ru["steps"], weights=xu.n_paths))}
     return {"value": paths / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{n_texels} texels x 81 bands x 4096 paths ({paths} paths) of the "
-                      f"spectral workload, FP64, {dt:.1f} s"}
+                      f"spectral workload, FP64, {dt:.1f} s",
+            "other_configs": per_config}
 
 
 def run_pipeline(args):

@@ -91,6 +91,35 @@ def test_independent_streams_agree_statistically(api):
     assert np.abs(zb).max() <= 5.0 and np.mean(np.abs(zb) <= 4.0) >= 0.995
 
 
+def test_precision_report_per_tally(api):
+    # The FP32 walk's error against the FP64 oracle, per tally, on the
+    # 16-set single-wavelength batch (2^18 paths) and on a spectral batch
+    # (n = 1.4, Fresnel faces): on the same random streams (rounding only:
+    # relative error) and on independent streams (statistics: z-scores).
+    cases = [("single-wavelength", inputs.single_wavelength(param_seed=0, n_paths=1 << 18), 32),
+             ("spectral", inputs.spectral_field(n_texels=2, param_seed=12, n_paths=1 << 15), 64)]
+    lines = []
+    for name, x, nb in cases:
+        o = opts(api, nbins=nb, r_max_mm=10.0, seed=4242)
+        g, code, _ = run_gpu(x, o)
+        assert code == 0
+        same = run_oracle(x, o)
+        indep = run_oracle(x, opts(api, nbins=nb, r_max_mm=10.0, seed=9191))
+        for key in ("R", "T", "A", "R1", "bins", "R_k"):
+            a, b, c = np.asarray(g[key]), np.asarray(same[key]), np.asarray(indep[key])
+            big = np.abs(b) > 1e-3
+            rel = np.abs(a - b)[big] / np.abs(b)[big] if big.any() else np.zeros(1)
+            se = np.hypot(np.asarray(same["se_" + key]), np.asarray(indep["se_" + key]))
+            m = se > 0
+            z = (a - c)[m] / se[m] if m.any() else np.zeros(1)
+            lines.append(f"{name:17s} {key:4s} same-stream rel err median {np.median(rel):.1e} "
+                         f"max {rel.max():.1e} | independent |z| rms {np.sqrt(np.mean(z ** 2)):.2f} "
+                         f"max {np.abs(z).max():.2f} (n={z.size})")
+            assert rel.max() < 1e-3, (name, key)
+            assert np.sqrt(np.mean(z ** 2)) < 1.3, (name, key)
+    print("\n" + "\n".join(lines))
+
+
 def test_cosine_lobe_incidence_parity(api):
     # cosine-weighted entry (third Philox draw per path): same-stream parity
     # with the oracle, and the closed form for the index-matched sets
