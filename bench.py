@@ -214,6 +214,7 @@ def run_pipeline(args):
     t_dec, t_walk = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
     # oracle pipeline on the first 32 x 32 texels (rows of the texture)
     sub = 32 * 32
+    t_or = time.perf_counter()
     ref = dec_ref.decode(rgb_np[:sub], W, bf16_activations=True)
     Tb = sub
     ids = (np.arange(81)[:, None] * T + np.arange(sub)[None, :]).reshape(-1)
@@ -221,6 +222,7 @@ def run_pipeline(args):
                        ref["g"].astype(np.float32), ref["w"].astype(np.float32),
                        np.full(81 * Tb, 1024, np.uint32), None, 1.4,
                        oracle.OracleOpts(nbins=64, r_max_mm=10.0, seed=1004), inst_ids=ids)
+    t_or = time.perf_counter() - t_or
     R = out["R"].cpu().numpy()[ids]
     se = np.sqrt(refw["se_R"] ** 2 + out["stderr_R"].cpu().numpy()[ids] ** 2)
     z = (R - refw["R"]) / np.maximum(se, 1e-12)
@@ -232,7 +234,11 @@ def run_pipeline(args):
             "subset": "32x32 texels x 81 bands vs FP64 oracle decoder + oracle walk",
             "R_z_abs_max": float(np.abs(z).max()), "R_z_rms": float(np.sqrt((z ** 2).mean())),
             "R_rel_err_median": float(np.median(np.abs(R - refw["R"]) / refw["R"])),
-            "frac_within_4sigma": float((np.abs(z) <= 4).mean())}
+            "frac_within_4sigma": float((np.abs(z) <= 4).mean()),
+            "cpu_baseline": {"value": 81.0 * sub * 1024 / t_or, "unit": "paths/s",
+                             "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"the 32x32-texel subset: FP64 decoder and walk, "
+                                       f"{81 * sub * 1024} paths, {t_or:.1f} s"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -630,7 +636,7 @@ def main():
         WORKLOAD["texels"] == 256 * 256 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "walk_persistent_kernel<false>",
+                "kernel": "walk_persistent_kernel<false, false, 0>",
                 "peak_basis": f"{sms} SMs x {SM_LANES_PER_CLK} FP32/INT32 lanes/clk x "
                               f"{f_mhz:.0f} MHz (median SM clock sampled in the timed region)",
                 "ops_per_step": ALG_ALU_OPS_PER_STEP, "steps_per_launch": total_draws,
