@@ -338,6 +338,19 @@ sss_status sss_decode(const float* rgb, int64_t T, const void* packed, void* wor
                       size_t workspace_bytes, float* alpha, float* g, float* sigma_t, float* w,
                       sss_stream_t stream);
 
+/* Self-test of the decoder's failure detection (no counterpart in the
+ * paper).  Launches one block whose first thread waits, with the same
+ * bounded mbarrier wait the decoder's pipeline roles use, for a barrier
+ * phase that nothing completes.  After limit_cycles SM clock cycles
+ * (1 <= limit_cycles <= 4e9, about 2 s at most) it gives up, sets
+ * SSS_FLAG_TIMEOUT in the word at `status` (device, 4-byte aligned, caller
+ * owned; a decode workspace's first word works), and returns: the context
+ * stays usable and sss_read_status on that word reports SSS_ERR_TIMEOUT.
+ * Errors: SSS_ERR_INVALID_ARG for a null or misaligned pointer or a limit
+ * out of range; SSS_ERR_CUDA if the launch fails. */
+sss_status sss_selftest_bounded_wait(uint32_t* status, int64_t limit_cycles,
+                                     sss_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * LUT-based mixture fit (paper Sec. 4.2, Eq. 6-9).  Tables of a homogeneous
  * semi-infinite medium at sigma_t = 1 (built with sss_walk, K = 1):

@@ -94,6 +94,8 @@ def _load():
     lib.sss_probe.restype = C.c_int
     lib.sss_probe_ops_per_thread_iter.argtypes = [C.c_int32]
     lib.sss_probe_ops_per_thread_iter.restype = C.c_int64
+    lib.sss_selftest_bounded_wait.argtypes = [C.c_void_p, C.c_int64, C.c_void_p]
+    lib.sss_selftest_bounded_wait.restype = C.c_int
     lib.sss_abi_version.argtypes = []
     lib.sss_abi_version.restype = C.c_int32
     if lib.sss_abi_version() != ABI_VERSION:
@@ -478,3 +480,11 @@ def probe(kind: str, iters: int, blocks: int, sink: torch.Tensor, stream=None) -
     assert sink.is_cuda and sink.dtype == torch.float32 and sink.numel() >= blocks * 256
     _check(lib.sss_probe(k, iters, blocks, _ptr(sink), _stream(stream)), "sss_probe")
     return blocks * 256 * iters * lib.sss_probe_ops_per_thread_iter(k)
+
+
+def selftest_bounded_wait(status: torch.Tensor, limit_cycles: int, stream=None) -> None:
+    """sss_selftest_bounded_wait on a CUDA int32/uint8 tensor whose first 4
+    bytes hold the status word (e.g. a decode workspace)."""
+    assert status.is_cuda
+    _check(lib.sss_selftest_bounded_wait(_ptr(status), limit_cycles, _stream(stream)),
+           "sss_selftest_bounded_wait")

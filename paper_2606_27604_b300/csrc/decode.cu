@@ -51,7 +51,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 }
 
 // Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitCycles) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
   while (true) {
@@ -63,7 +64,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -553,6 +554,24 @@ __global__ void pack_weights_kernel(const __nv_bfloat16* __restrict__ src, int s
   const bool ok = sr >= 0 && sr < src_rows && sc >= 0 && sc < src_cols;
   dst[i] = ok ? src[(size_t)sr * src_cols + sc] : __float2bfloat16_rn(0.0f);
   if (c == 0 && bdst) bdst[r] = (sr >= 0 && sr < src_rows) ? bsrc[sr] : 0.0f;
+}
+
+// ------------------------------------------------ bounded-wait self-test --
+// One thread waits, with the pipeline's bounded wait, for a phase of an
+// mbarrier that nothing completes; when the limit runs out it records the
+// timeout in the status word exactly as the GEMM roles do, and returns.
+__global__ void bounded_wait_selftest_kernel(unsigned int* status, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0u, limit)) atomicOr(status, DEC_FLAG_TIMEOUT);
+  }
+}
+
+cudaError_t launch_bounded_wait_selftest(unsigned int* status, long long limit, cudaStream_t st) {
+  bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(status, limit);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- launch --

@@ -151,6 +151,18 @@ sss_status sss_decoder_pack(const sss_decoder_weights* w, void* packed, size_t p
   return SSS_OK;
 }
 
+sss_status sss_selftest_bounded_wait(uint32_t* status, int64_t limit_cycles,
+                                     sss_stream_t stream) {
+  if (!status || (reinterpret_cast<uintptr_t>(status) & 3u) || limit_cycles < 1 ||
+      limit_cycles > 4000000000LL)
+    return SSS_ERR_INVALID_ARG;
+  cudaGetLastError();
+  return launch_bounded_wait_selftest(reinterpret_cast<unsigned int*>(status), limit_cycles,
+                                      static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? SSS_OK
+             : SSS_ERR_CUDA;
+}
+
 sss_status sss_decode(const float* rgb, int64_t T, const void* packed, void* workspace,
                       size_t workspace_bytes, float* alpha, float* g, float* sigma_t, float* w,
                       sss_stream_t stream) {

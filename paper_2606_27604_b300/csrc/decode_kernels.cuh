@@ -48,6 +48,8 @@ struct EpiParams {
   long long M;
 };
 
+cudaError_t launch_bounded_wait_selftest(unsigned int* status, long long limit,
+                                         cudaStream_t st);
 cudaError_t launch_gemm(int bn, int epi, int cm, const CUtensorMap& ta, const CUtensorMap& tb,
                         int a_x0, int num_kb, int n_tiles, long long m_tiles, const float* bias,
                         const EpiParams& ep, unsigned int* status, cudaStream_t st);

@@ -70,3 +70,22 @@ def test_decode_feeds_the_walk(api):
     code, flags = api.read_status(r["_workspace"])
     assert code == 0, flags
     assert torch.all(r["R"] > 0) and torch.all(r["R"] < 1)
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(api):
+    # Failure detection without a fault: a wait on an mbarrier phase that
+    # nothing completes, with the pipeline's own bounded wait and a ~1 ms
+    # limit, records the timeout in the status word and returns; the next
+    # decode on the same context runs clean.
+    import torch
+    status = torch.zeros(64, dtype=torch.int32, device="cuda")
+    api.selftest_bounded_wait(status, 2_000_000)
+    torch.cuda.synchronize()
+    code, flags = api.read_status(status)
+    assert flags & 0x10 and code == 8, (code, flags)
+    W = inputs.decoder_weights(seed=4)
+    g, code, flags = _run(api, inputs.rgb_texture(side=4, seed=4), W)
+    assert code == 0 and flags == 0
+    assert np.isfinite(g["alpha"]).all()
+    with pytest.raises(api.SSSError):
+        api.selftest_bounded_wait(status, 0)
