@@ -57,7 +57,9 @@ class _Out(C.Structure):
 PATH_DTYPE = np.dtype([("exit_kind", np.int32), ("medium", np.int32), ("bin", np.int32),
                        ("weight", np.float64), ("absorbed", np.float64),
                        ("steps", np.uint32), ("n_coll", np.uint32), ("length", np.float64),
-                       ("dlogp_dg", np.float64), ("x", np.float64), ("y", np.float64)],
+                       ("dlogp_dg", np.float64), ("x", np.float64), ("y", np.float64),
+                       ("n_coll2", np.uint32), ("length2", np.float64),
+                       ("dlogp_dg2", np.float64)],
                       align=True)
 
 
@@ -214,10 +216,17 @@ def walk_hero(alpha, sigma_t, g, w, n_paths_per_group: int, hero: int, bands_per
 
 def walk_grad(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
               opts: OracleOpts = OracleOpts(), grad_R=None, grad_bins=None,
-              grad_R_k=None, grad_T=None, inst_ids=None) -> dict:
+              grad_R_k=None, grad_T=None, inst_ids=None, layer2=None) -> dict:
     """Score-function gradient of sum(upstream * tallies) w.r.t. the
-    per-medium parameters, shape [K][n_inst] each, with standard errors."""
+    per-medium parameters, shape [K][n_inst] each, with standard errors.
+    With ``layer2`` (as in ``walk``) the per-medium terms cover the top layer
+    and d_alpha2, d_sigma_t2, d_g2 ([n_inst]) the second layer's optics."""
     alpha, sigma_t, g, w, K, n = _check(alpha, sigma_t, g, w)
+    l2 = None
+    keep = None
+    if layer2 is not None:
+        keep = [_f32(a) for a in layer2]
+        l2 = _Layer2(*(_p(k) for k in keep))
     n_paths = np.ascontiguousarray(n_paths, dtype=np.uint32)
     th = None if thickness_mm is None else _f32(thickness_mm)
 
@@ -233,13 +242,18 @@ def walk_grad(alpha, sigma_t, g, w, n_paths, thickness_mm=None, n_rel=1.0,
     gT = f64(grad_T, (n,))
     res = {k: np.zeros((K, n)) for k in ("d_alpha", "d_sigma_t", "d_g", "d_w",
                                          "se_d_alpha", "se_d_sigma_t", "se_d_g", "se_d_w")}
+    for k in ("d_alpha2", "d_sigma_t2", "d_g2", "se_d_alpha2", "se_d_sigma_t2", "se_d_g2"):
+        res[k] = np.zeros(n)
     o = opts._c()
     rc = _load().oracle_walk_grad(
         C.c_int64(n), C.c_int(K), _p(alpha), _p(sigma_t), _p(g), _p(w), _p(n_paths),
         _p(th), C.c_double(n_rel), C.byref(o), _p(_ids(inst_ids, n)),
+        C.byref(l2) if l2 is not None else None,
         _p(gR), _p(gB), _p(gK), _p(gT),
         *[_p(res[k]) for k in ("d_alpha", "d_sigma_t", "d_g", "d_w",
-                               "se_d_alpha", "se_d_sigma_t", "se_d_g", "se_d_w")])
+                               "se_d_alpha", "se_d_sigma_t", "se_d_g", "se_d_w",
+                               "d_alpha2", "d_sigma_t2", "d_g2",
+                               "se_d_alpha2", "se_d_sigma_t2", "se_d_g2")])
     if rc != 0:
         raise ValueError("oracle_walk_grad rejected its arguments")
     return res

@@ -204,6 +204,10 @@ typedef struct {
   double length;    /* total distance travelled inside the medium, mm */
   double dlogp_dg;  /* sum over scatterings of d log p_HG / dg */
   double x, y;      /* exit point on the face */
+  /* the parts of n_coll, length and dlogp_dg spent in the second layer of a
+   * two-layer slab (0 otherwise) */
+  uint32_t n_coll2;
+  double length2, dlogp_dg2;
 } oracle_path;
 
 /* inst indexes the parameter arrays; rng_inst is the instance number the
@@ -286,6 +290,7 @@ void oracle_trace_path_layered(const float* alpha, const float* sigma_t, const f
       pos[1] += db * dir[1];
       int top = dir[2] < 0.0;
       res->length += db;
+      if (layer == 1) res->length2 += db;
       if (l2 && ((top && layer == 1) || (!top && layer == 0))) {
         /* Internal interface (index matched): cross into the other layer
          * and draw a fresh flight there (flights are memoryless). */
@@ -324,6 +329,10 @@ void oracle_trace_path_layered(const float* alpha, const float* sigma_t, const f
     for (int i = 0; i < 3; ++i) pos[i] += s * dir[i];
     res->length += s;
     res->n_coll++;
+    if (layer == 1) {
+      res->length2 += s;
+      res->n_coll2++;
+    }
     if (o->mode == 0) {
       res->absorbed += W * (1.0 - a);
       W *= a;
@@ -335,7 +344,9 @@ void oracle_trace_path_layered(const float* alpha, const float* sigma_t, const f
       if (u[3] >= a) { res->absorbed += W; res->exit_kind = 2; break; }
     }
     double mu = oracle_hg_mu(gg, u[1]);
-    res->dlogp_dg += oracle_hg_dlogp_dg(gg, mu);
+    const double dl = oracle_hg_dlogp_dg(gg, mu);
+    res->dlogp_dg += dl;
+    if (layer == 1) res->dlogp_dg2 += dl;
     oracle_rotate(dir, mu, 2.0 * M_PI * u[2]);
   }
   res->steps = step;
@@ -708,17 +719,25 @@ int oracle_walk_hero(int64_t n_inst, int K, const float* alpha, const float* sig
  * whose conditional mean given the geometry is the analog throughput, so
  * they add no score term.  Outputs d_* are [K][n_inst] and hold the mean
  * over the instance's N paths. */
+/* With a second layer (l2 non-NULL), the score terms above take only the
+ * collisions, length and scatterings of the top layer (the chosen medium),
+ * and the layer's own optics get the same three terms from its part of the
+ * path: d_alpha2, d_sigma_t2, d_g2 and their standard errors se_d_*2
+ * ([n_inst] each, or NULL). */
+#define ORC_NG (4 * ORC_KMAX + 3) /* per-path score vector: [4][K] then 3 for layer 2 */
 int oracle_walk_grad(int64_t n_inst, int K, const float* alpha, const float* sigma_t,
                      const float* g, const float* w, const uint32_t* n_paths,
                      const float* thickness_mm, double n_rel, const oracle_opts* o,
-                     const int64_t* inst_ids,
+                     const int64_t* inst_ids, const oracle_layer2* l2,
                      const double* grad_R, const double* grad_bins,
                      const double* grad_R_k, const double* grad_T,
                      double* d_alpha, double* d_sigma_t, double* d_g, double* d_w,
                      double* se_d_alpha, double* se_d_sigma_t, double* se_d_g,
-                     double* se_d_w) {
+                     double* se_d_w, double* d_alpha2, double* d_sigma_t2, double* d_g2,
+                     double* se_d_alpha2, double* se_d_sigma_t2, double* se_d_g2) {
   if (K < 1 || K > ORC_KMAX || o->nbins < 1) return 1;
   const int nb = o->nbins;
+  const int ng = 4 * K + 3;
   for (int64_t i = 0; i < n_inst; ++i) {
     const uint32_t N = n_paths[i];
     const double d = thickness_mm ? (double)thickness_mm[i] : INFINITY;
@@ -726,17 +745,17 @@ int oracle_walk_grad(int64_t n_inst, int K, const float* alpha, const float* sig
     float wk[ORC_KMAX];
     for (int k = 0; k < K; ++k) { wk[k] = w[(int64_t)k * n_inst + i]; wsum += wk[k]; }
     const int64_t nch = ((int64_t)N + ORC_CHUNK - 1) / ORC_CHUNK;
-    double* ps = calloc((size_t)(nch > 0 ? nch : 1) * 8 * ORC_KMAX, sizeof(double));
+    double* ps = calloc((size_t)(nch > 0 ? nch : 1) * 2 * ORC_NG, sizeof(double));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t ch = 0; ch < nch; ++ch) {
-      double* ls = ps + (size_t)ch * 8 * ORC_KMAX;
-      double* ls2 = ls + 4 * ORC_KMAX;
+      double* ls = ps + (size_t)ch * 2 * ORC_NG;
+      double* ls2 = ls + ORC_NG;
       const int64_t p1 = (ch + 1) * ORC_CHUNK < (int64_t)N ? (ch + 1) * ORC_CHUNK : (int64_t)N;
       for (int64_t p = ch * ORC_CHUNK; p < p1; ++p) {
         oracle_path r;
-        oracle_trace_path(alpha, sigma_t, g, w, K, n_inst, i,
-                          inst_ids ? (uint32_t)inst_ids[i] : (uint32_t)i, (uint32_t)p, d,
-                          n_rel, o, &r);
+        oracle_trace_path_layered(alpha, sigma_t, g, w, K, n_inst, i,
+                                  inst_ids ? (uint32_t)inst_ids[i] : (uint32_t)i, (uint32_t)p,
+                                  d, n_rel, o, l2, &r);
         double v = 0.0;
         if (r.exit_kind == 0) {
           if (grad_R) v += grad_R[i];
@@ -745,28 +764,42 @@ int oracle_walk_grad(int64_t n_inst, int K, const float* alpha, const float* sig
         } else if (r.exit_kind == 1) {
           if (grad_T) v += grad_T[i];
         }
-        double c[4 * ORC_KMAX] = {0};
+        double c[ORC_NG] = {0};
         if (v != 0.0 && r.weight != 0.0) {
           const int k = r.medium;
           const double a = alpha[(int64_t)k * n_inst + i];
           const double st = sigma_t[(int64_t)k * n_inst + i];
           const double Wv = r.weight * v;
-          c[0 * K + k] = Wv * (double)r.n_coll / a;
-          c[1 * K + k] = Wv * ((double)r.n_coll / st - r.length);
-          c[2 * K + k] = Wv * r.dlogp_dg;
+          /* top layer (the whole path without a second layer) */
+          const double n1 = (double)(r.n_coll - r.n_coll2);
+          c[0 * K + k] = Wv * n1 / a;
+          c[1 * K + k] = Wv * (n1 / st - (r.length - r.length2));
+          c[2 * K + k] = Wv * (r.dlogp_dg - r.dlogp_dg2);
           c[3 * K + k] = Wv * wsum / (double)wk[k];
+          if (l2) {
+            const double n2 = (double)r.n_coll2;
+            c[4 * K + 0] = Wv * n2 / (double)l2->alpha2[i];
+            c[4 * K + 1] = Wv * (n2 / (double)l2->sigma_t2[i] - r.length2);
+            c[4 * K + 2] = Wv * r.dlogp_dg2;
+          }
         }
-        for (int j = 0; j < 4 * K; ++j) { ls[j] += c[j]; ls2[j] += c[j] * c[j]; }
+        for (int j = 0; j < ng; ++j) { ls[j] += c[j]; ls2[j] += c[j] * c[j]; }
       }
     }
-    double s[4 * ORC_KMAX] = {0}, s2[4 * ORC_KMAX] = {0};
+    double s[ORC_NG] = {0}, s2[ORC_NG] = {0};
     for (int64_t ch = 0; ch < nch; ++ch)
-      for (int j = 0; j < 4 * K; ++j) {
-        s[j] += ps[(size_t)ch * 8 * ORC_KMAX + (size_t)j];
-        s2[j] += ps[(size_t)ch * 8 * ORC_KMAX + 4 * ORC_KMAX + (size_t)j];
+      for (int j = 0; j < ng; ++j) {
+        s[j] += ps[(size_t)ch * 2 * ORC_NG + (size_t)j];
+        s2[j] += ps[(size_t)ch * 2 * ORC_NG + ORC_NG + (size_t)j];
       }
     free(ps);
     const double n = (double)N;
+    if (d_alpha2) d_alpha2[i] = s[4 * K + 0] / n;
+    if (d_sigma_t2) d_sigma_t2[i] = s[4 * K + 1] / n;
+    if (d_g2) d_g2[i] = s[4 * K + 2] / n;
+    if (se_d_alpha2) se_d_alpha2[i] = se_of(s[4 * K + 0], s2[4 * K + 0], n);
+    if (se_d_sigma_t2) se_d_sigma_t2[i] = se_of(s[4 * K + 1], s2[4 * K + 1], n);
+    if (se_d_g2) se_d_g2[i] = se_of(s[4 * K + 2], s2[4 * K + 2], n);
     double* outs[4] = {d_alpha, d_sigma_t, d_g, d_w};
     double* ses[4] = {se_d_alpha, se_d_sigma_t, se_d_g, se_d_w};
     for (int q = 0; q < 4; ++q)

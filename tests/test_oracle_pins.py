@@ -463,6 +463,53 @@ def test_log_bins_partition_the_same_exits():
     np.testing.assert_allclose(lg["overflow"], lin["overflow"], rtol=1e-12)
 
 
+def test_two_layer_gradient_pins():
+    # gradients of the two-layer walk (score form, Sec. 4.1 path
+    # contribution): (1) an interface too deep to reach gives zero layer-2
+    # gradients and the one-layer gradients exactly; (2) without roulette the
+    # paths do not depend on the albedos, so a central difference of R in
+    # alpha2 on the same streams equals the score estimate; (3) with equal
+    # optics in both layers, top-layer plus layer-2 gradients add up to the
+    # one-layer gradient of that medium (statistically).
+    K = 1
+    a = np.array([[0.9]], np.float32); s_ = np.array([[4.0]], np.float32)
+    g = np.array([[0.6]], np.float32); w = np.ones((1, 1), np.float32)
+    N = np.array([40000], np.uint32)
+    up = dict(grad_R=np.ones(1))
+    o = oracle.OracleOpts(nbins=8, r_max_mm=5.0, seed=41)
+    deep = (np.array([0.99], np.float32), np.array([2.0], np.float32),
+            np.array([0.3], np.float32), np.array([1e4], np.float32))
+    gd = oracle.walk_grad(a, s_, g, w, N, None, 1.4, o, layer2=deep, **up)
+    g1 = oracle.walk_grad(a, s_, g, w, N, None, 1.4, o, **up)
+    for k in ("d_alpha", "d_sigma_t", "d_g", "d_w"):
+        np.testing.assert_array_equal(gd[k], g1[k])
+    assert gd["d_alpha2"][0] == 0 and gd["d_sigma_t2"][0] == 0 and gd["d_g2"][0] == 0
+    # (2) alpha2 by central difference, roulette off
+    o0 = oracle.OracleOpts(nbins=8, r_max_mm=5.0, seed=42, rr_threshold=0.0)
+    l2 = (np.array([0.95], np.float32), np.array([2.0], np.float32),
+          np.array([0.3], np.float32), np.array([0.15], np.float32))
+    gs = oracle.walk_grad(a, s_, g, w, N, None, 1.4, o0, layer2=l2, **up)
+    h = 1e-3
+    lo = (l2[0] - np.float32(h), *l2[1:]); hi = (l2[0] + np.float32(h), *l2[1:])
+    Rlo = oracle.walk(a, s_, g, w, N, None, 1.4, o0, layer2=lo)["R"][0]
+    Rhi = oracle.walk(a, s_, g, w, N, None, 1.4, o0, layer2=hi)["R"][0]
+    fd = (Rhi - Rlo) / (float(hi[0][0]) - float(lo[0][0]))
+    print("d R / d alpha2: score", gs["d_alpha2"][0], "central difference", fd)
+    assert abs(gs["d_alpha2"][0] - fd) <= 1e-3 * abs(fd)
+    # (3) sum rule with equal layers
+    same = (a[0].copy(), s_[0].copy(), g[0].copy(), np.array([0.25], np.float32))
+    N2 = np.array([200000], np.uint32)
+    two = oracle.walk_grad(a, s_, g, w, N2, None, 1.4, o, layer2=same, **up)
+    one = oracle.walk_grad(a, s_, g, w, N2, None, 1.4, oracle.OracleOpts(nbins=8, r_max_mm=5.0,
+                                                                        seed=43), **up)
+    for k, k2 in (("d_alpha", "d_alpha2"), ("d_sigma_t", "d_sigma_t2"), ("d_g", "d_g2")):
+        tot = two[k][0, 0] + two[k2][0]
+        # sd(X + Y) <= sd(X) + sd(Y) whatever the correlation of the parts
+        se = np.hypot(two["se_" + k][0, 0] + two["se_" + k2][0], one["se_" + k][0, 0])
+        print(k, "top + layer 2", tot, "one layer", one[k][0, 0], "se", se)
+        assert abs(tot - one[k][0, 0]) <= Z * se, k
+
+
 def test_two_layer_limits_and_ballistic_transmittance():
     N = np.array([100000], np.uint32)
     o = oracle.OracleOpts(nbins=16, r_max_mm=4.0, seed=21)
