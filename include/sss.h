@@ -82,8 +82,9 @@ typedef void* sss_stream_t; /* cudaStream_t */
  *          the top layer 0 <= z < d1_mm, this second layer fills
  *          d1_mm <= z < thickness (semi-infinite if thickness is +inf).  The
  *          interface is index matched: a flight that reaches it stops there
- *          and continues with a fresh flight in the other layer.  Forward
- *          only (sss_walk_bwd returns SSS_ERR_UNSUPPORTED). */
+ *          and continues with a fresh flight in the other layer.
+ *          sss_walk_bwd gives the second layer's gradients in
+ *          sss_grad_out.d_alpha2 / d_sigma_t2 / d_g2. */
 typedef struct {
   const float* alpha;
   const float* sigma_t;
@@ -239,12 +240,19 @@ typedef struct {
 /* Parameter gradients, float64 device [K][n_inst], any may be NULL.
  * d_w is the partial derivative of sum_k w_k S_k with the other weights
  * held fixed (Eq. 4), i.e. the medium's own contribution S_k; project onto
- * the simplex (subtract the w-weighted mean) for a constrained step. */
+ * the simplex (subtract the w-weighted mean) for a constrained step.
+ * Two-layer slabs: d_alpha .. d_w cover the top layer (the chosen medium),
+ * and d_alpha2, d_sigma_t2, d_g2 ([n_inst] float64 device, any may be NULL)
+ * the second layer's optics; those three are ignored without a second
+ * layer. */
 typedef struct {
   double* d_alpha;
   double* d_sigma_t;
   double* d_g;
   double* d_w;
+  double* d_alpha2;
+  double* d_sigma_t2;
+  double* d_g2;
 } sss_grad_out;
 
 /* Fill *o with the defaults: 64 bins over 10 mm, mode 0, W_th = 1/16,

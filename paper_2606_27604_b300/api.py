@@ -59,8 +59,11 @@ class GradIn(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("grad_R", "grad_bins", "grad_R_k", "grad_T")]
 
 
+GRAD_KEYS = ("d_alpha", "d_sigma_t", "d_g", "d_w", "d_alpha2", "d_sigma_t2", "d_g2")
+
+
 class GradOut(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("d_alpha", "d_sigma_t", "d_g", "d_w")]
+    _fields_ = [(n, C.c_void_p) for n in GRAD_KEYS]
 
 
 def _load():
@@ -269,18 +272,23 @@ def walk(m: Media, o: WalkOptions, workspace: Optional[torch.Tensor] = None,
 def walk_bwd(m: Media, o: WalkOptions, grad_R=None, grad_bins=None, grad_R_k=None,
              grad_T=None, workspace: Optional[torch.Tensor] = None, out: Optional[dict] = None,
              stream=None) -> dict:
-    """Path-replay adjoint (sss_walk_bwd): d(sum upstream * tallies)/d(media)."""
+    """Path-replay adjoint (sss_walk_bwd): d(sum upstream * tallies)/d(media).
+    With a second layer the result also holds d_alpha2, d_sigma_t2, d_g2
+    ([n_inst]) for the layer's optics."""
     if workspace is None:
         workspace = alloc_workspace(m, o, adjoint=True)
     dev = m.alpha.device
     if out is None:
         out = {k: torch.empty(m.K, m.n_inst, dtype=torch.float64, device=dev)
                for k in ("d_alpha", "d_sigma_t", "d_g", "d_w")}
+        if m.layer2 is not None:
+            for k in ("d_alpha2", "d_sigma_t2", "d_g2"):
+                out[k] = torch.empty(m.n_inst, dtype=torch.float64, device=dev)
     for g in (grad_R, grad_bins, grad_R_k, grad_T):
         if g is not None:
             assert g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()
     gi = GradIn(_ptr(grad_R), _ptr(grad_bins), _ptr(grad_R_k), _ptr(grad_T))
-    go = GradOut(*(_ptr(out.get(k)) for k in ("d_alpha", "d_sigma_t", "d_g", "d_w")))
+    go = GradOut(*(_ptr(out.get(k)) for k in GRAD_KEYS))
     p, oc = m.c(), o.c()
     _check(lib.sss_walk_bwd(C.byref(p), C.byref(oc), _ptr(workspace), workspace.numel(),
                             C.byref(gi), C.byref(go), _stream(stream)), "sss_walk_bwd")

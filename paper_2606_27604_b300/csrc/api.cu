@@ -93,8 +93,9 @@ Layout make_layout(const sss_params* p, const sss_walk_opts* o, bool adj) {
   }
   L.acc = off;
   if (adj) {
-    L.acc_words = 4 * p->K;
-    off += align_up((size_t)4 * p->K * n * 8);
+    // [4][K] per-medium gradient words, then 3 for a second layer's optics
+    L.acc_words = 4 * p->K + (p->alpha2 ? 3 : 0);
+    off += align_up((size_t)L.acc_words * n * 8);
   } else {
     L.acc_words = tally_count(o->nbins, p->K, o->want_sumsq);
     off += align_up((size_t)L.acc_words * n * 8);
@@ -330,6 +331,9 @@ sss_status enqueue_walk(bool adj, const sss_params* p, const sss_walk_opts* o, v
     if (gout) {
       go.d_alpha = gout->d_alpha; go.d_sigma_t = gout->d_sigma_t;
       go.d_g = gout->d_g; go.d_w = gout->d_w;
+      if (p->alpha2) {
+        go.d_alpha2 = gout->d_alpha2; go.d_sigma_t2 = gout->d_sigma_t2; go.d_g2 = gout->d_g2;
+      }
     }
     go.status = status;
     launch_finalize_grads(c, gi, acc, go, st);
@@ -347,7 +351,6 @@ sss_status run(bool adj, const sss_params* p, const sss_walk_opts* o, void* ws, 
     return SSS_ERR_INVALID_ARG;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1))) return SSS_ERR_INVALID_ARG;
   if (adj && !gout) return SSS_ERR_INVALID_ARG;
-  if (adj && p->alpha2) return SSS_ERR_UNSUPPORTED;  // two-layer slabs: forward only
   if (o->hero_bands > 0) {
     // hero-wavelength sharing: forward, persistent schedule, one layer,
     // uniform path budgets, whole texels

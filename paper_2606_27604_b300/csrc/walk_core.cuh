@@ -111,8 +111,10 @@ struct Path {
   uint32_t step, path, inst, n_coll;
   uint32_t cinst;  // instance number in the random-number counters
   int k;
-  float L;        // path length inside the medium (adjoint)
-  float G;        // sum of d log p_HG / d g (adjoint)
+  float L;        // path length inside the medium (adjoint; top layer if layered)
+  float G;        // sum of d log p_HG / d g (adjoint; top layer if layered)
+  uint32_t n2;    // two-layer adjoint: collisions, length and HG score in the
+  float L2, G2;   // second layer (n_coll counts both layers)
   // two-layer slab: optics of the other layer, interface depth, current layer
   float a_o, fl_o, g_o, sigt_o, d1;
   int layer;
@@ -269,6 +271,9 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.G = 0.0f;
   if (LAYERED) {
     p.layer = 0;
+    p.n2 = 0u;
+    p.L2 = 0.0f;
+    p.G2 = 0.0f;
     p.d1 = __ldg(c.d1 + inst);
     p.a_o = __ldg(c.alpha2 + inst);
     p.sigt_o = __ldg(c.sigma_t2 + inst);
@@ -338,7 +343,10 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
   p.x = xy.x;
   p.y = xy.y;
   p.z = hit ? (cross ? p.d1 : (top ? 0.0f : p.d)) : __fmaf_rn(dist, p.uz, p.z);
-  if (ADJ) p.L = __fadd_rn(p.L, dist);
+  if (ADJ) {
+    if (LAYERED && p.layer) p.L2 = __fadd_rn(p.L2, dist);
+    else p.L = __fadd_rn(p.L, dist);
+  }
 
   // Face: smooth-dielectric Fresnel, reflect with probability F.
   const float F = fresnel(fabsf(p.uz), c.n_rel);
@@ -381,6 +389,7 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
     p.Aacc = dead ? __fadd_rn(p.Aacc, p.W) : p.Aacc;
   }
   p.n_coll += hit ? 0u : 1u;
+  if (ADJ && LAYERED) p.n2 += (hit || !p.layer) ? 0u : 1u;
 
   // Henyey-Greenstein scattering with this medium's g.
   const float mu = hg_mu(p.g, u1);
@@ -396,7 +405,11 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
       hs.D[m] = __fmaf_rn(scat, __fmaf_rn(-1.5f, __fsub_rn(lm, lh), hs.cg[m]), hs.D[m]);
     }
   }
-  if (ADJ) p.G = (hit || dead) ? p.G : __fadd_rn(p.G, hg_dlogp_dg(p.g, mu));
+  if (ADJ) {
+    const float dl = (hit || dead) ? 0.0f : hg_dlogp_dg(p.g, mu);
+    if (LAYERED && p.layer) p.G2 = __fadd_rn(p.G2, dl);
+    else p.G = __fadd_rn(p.G, dl);
+  }
   // Azimuth phi = 2 pi u2; evaluated as phi - pi in (-pi, pi), then negated.
   float sp, cp;
   sincos_approx(__fmul_rn(6.2831853071795865f, __fsub_rn(u2, 0.5f)), &sp, &cp);

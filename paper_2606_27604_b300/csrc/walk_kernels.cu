@@ -213,7 +213,7 @@ enum : int { LANE_IDLE = 0, LANE_RUNNING = 1, LANE_DONE = 2 };
 // Adds one finished path to its slot's shared accumulators, or, when the
 // slot has moved on to another unit (`direct`), straight to the instance's
 // global accumulators in the layout the slot flush uses.
-template <bool ADJ>
+template <bool ADJ, bool LAYERED>
 __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& s,
                                            const GradIn& gi, const TallyOut& t, const Path& p,
                                            int ev, unsigned long long* m, bool direct) {
@@ -253,20 +253,33 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
     }
     if (v != 0.0f && p.W != 0.0f) {  // (W = 0: a zero-weight medium, chosen uniformly)
       const float Wv = __fmul_rn(__fmul_rn(p.W, v), p.gscale);
-      const float nf = (float)p.n_coll;
-      float q[4];
-      q[0] = __fmul_rn(Wv, __fdiv_rn(nf, p.alpha));
-      q[1] = __fmul_rn(Wv, __fsub_rn(__fdiv_rn(nf, p.sigt), p.L));
+      // the top layer's optics (a path that ends in the second layer holds
+      // them as the "other" layer's)
+      const bool low = LAYERED && p.layer;
+      const float a1 = low ? p.a_o : p.alpha, s1 = low ? p.sigt_o : p.sigt;
+      const float nf = LAYERED ? (float)(p.n_coll - p.n2) : (float)p.n_coll;
+      constexpr int NQ = LAYERED ? 7 : 4;
+      float q[NQ];
+      q[0] = __fmul_rn(Wv, __fdiv_rn(nf, a1));
+      q[1] = __fmul_rn(Wv, __fsub_rn(__fdiv_rn(nf, s1), p.L));
       q[2] = __fmul_rn(Wv, p.G);
       q[3] = __fmul_rn(Wv, __fdiv_rn(p.wsum, __ldg(c.w + (size_t)p.k * c.n_inst + p.inst)));
+      if constexpr (LAYERED) {
+        const float a2 = low ? p.alpha : p.a_o, s2 = low ? p.sigt : p.sigt_o;
+        const float n2 = (float)p.n2;
+        q[4] = __fmul_rn(Wv, __fdiv_rn(n2, a2));
+        q[5] = __fmul_rn(Wv, __fsub_rn(__fdiv_rn(n2, s2), p.L2));
+        q[6] = __fmul_rn(Wv, p.G2);
+      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < NQ; ++j) {
         float x = q[j];
         if (!(fabsf(x) < p.glim)) {
           atomicOr(s.status, SSS_DEV_FLAG_OVERFLOW);
           x = (x != x) ? 0.0f : copysignf(p.glim, x);
         }
-        add(j * c.K + p.k, (unsigned long long)__float2ll_rn(x));
+        // words [4][K] per medium, then 3 for the second layer
+        add(j < 4 ? j * c.K + p.k : 4 * c.K + (j - 4), (unsigned long long)__float2ll_rn(x));
       }
     }
   }
@@ -385,8 +398,8 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
           tally_path_hero<HERO>(c, s, t, p, hs, ev, slot_mem + (size_t)myslot * slot_words,
                                 meta[myslot].gen != mygen);
         else
-          tally_path<ADJ>(c, s, gi, t, p, ev, slot_mem + (size_t)myslot * slot_words,
-                          meta[myslot].gen != mygen);
+          tally_path<ADJ, LAYERED>(c, s, gi, t, p, ev, slot_mem + (size_t)myslot * slot_words,
+                                   meta[myslot].gen != mygen);
         st = LANE_IDLE;
       }
       // ---- 2. refill idle lanes from the current unit (regrouping) ----
@@ -554,6 +567,12 @@ __global__ void finalize_grads_kernel(WalkConst c, GradIn gi, const unsigned lon
     for (int k = 0; k < c.K; ++k)
       if (c.w[(size_t)k * c.n_inst + i] == 0.0f) atomicOr(go.status, SSS_DEV_FLAG_ZERO_WEIGHT);
   }
+  if (c.alpha2) {  // second layer: words 4K .. 4K+2
+    double* outs2[3] = {go.d_alpha2, go.d_sigma_t2, go.d_g2};
+    for (int q = 0; q < 3; ++q)
+      if (outs2[q])
+        outs2[q][i] = (double)(long long)raw[(size_t)(4 * c.K + q) * c.n_inst + i] * scale;
+  }
 }
 
 // ------------------------------------------------------------ diagnostics --
@@ -603,7 +622,9 @@ void launch_walk_persistent(bool adj, int grid, int block, size_t smem, const Wa
 }
 
 const void* persistent_kernel_ptr(bool adj, bool layered, int hero) {
-  if (adj) return (const void*)walk_persistent_kernel<true, false, 0>;
+  if (adj)
+    return layered ? (const void*)walk_persistent_kernel<true, true, 0>
+                   : (const void*)walk_persistent_kernel<true, false, 0>;
   if (layered) return (const void*)walk_persistent_kernel<false, true, 0>;
   switch (hero) {
     case 1: return (const void*)walk_persistent_kernel<false, false, 1>;

@@ -50,6 +50,7 @@ struct GradIn {
 
 struct GradOut {
   double *d_alpha, *d_sigma_t, *d_g, *d_w;
+  double *d_alpha2, *d_sigma_t2, *d_g2;  // second layer of a two-layer slab
   unsigned int* status;
 };
 

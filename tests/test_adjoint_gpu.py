@@ -65,6 +65,57 @@ def test_adjoint_matches_oracle_score_gradient(api, select_pdf):
         assert ratio.max() <= 1.0, k
 
 
+def test_two_layer_adjoint_matches_oracle(api):
+    # two-layer slabs: the top-layer (mixture) gradients take only the
+    # top layer's part of each path and the second layer's optics get their
+    # own; same-stream parity with the oracle's score gradient for all of
+    # them, and a central difference in alpha2 without roulette
+    x = inputs.two_layer_batch(n_inst=48, param_seed=8, n_paths=1 << 13)
+    o = api.WalkOptions(nbins=32, r_max_mm=10.0, seed=1013)
+    up = _upstream(x, 32, seed=5)
+    g, code, flags = _grads_gpu(api, x, o, **up)
+    assert code == 0 and flags == 0
+    r = oracle.walk_grad(x.alpha, x.sigma_t, x.g, x.w, x.n_paths, None, x.n_rel,
+                         to_oracle_opts(o), layer2=x.layer2, **up)
+    for k in ("d_alpha", "d_sigma_t", "d_g", "d_w", "d_alpha2", "d_sigma_t2", "d_g2"):
+        a, b, se = g[k], r[k], r["se_" + k]
+        assert np.all(np.abs(a - b) <= 4 * math.sqrt(2) * se + 1e-12), k
+        tight = 1e-4 * np.abs(b) + 0.25 * se + 1e-12
+        ratio = np.abs(a - b) / tight
+        print("two-layer", k, "worst same-stream ratio", ratio.max())
+        assert ratio.max() <= 1.0, k
+    # alpha2: without roulette the paths do not depend on the albedos (a
+    # path that reaches the step cap is dropped alike by both estimates)
+    import torch
+    o0 = api.WalkOptions(nbins=32, r_max_mm=10.0, seed=1014, rr_threshold=0.0)
+    gs, code, _ = _grads_gpu(api, x, o0, grad_R=np.ones(x.n_inst))
+    assert code in (0, 4)   # OK or STEP_LIMIT
+    # steps that keep alpha2 +- h inside [0, 1] and small against the path
+    # length: R depends on alpha2 through alpha2^n with n up to thousands, so
+    # the central difference is accurate only for n h << 1
+    f0 = api.walk(api.Media.from_inputs(x), o0)
+    torch.cuda.synchronize()
+    steps = f0["steps"].cpu().numpy()
+    h = np.minimum(np.minimum(1e-3, 0.5 * (1 - x.layer2[0].astype(np.float64))),
+                   0.05 / np.maximum(steps, 1.0)).astype(np.float32)
+    Rs, a2s = [], []
+    for sgn in (-1, 1):
+        xs = x.subset(np.arange(x.n_inst))
+        a2 = (x.layer2[0] + np.float32(sgn) * h).astype(np.float32)
+        assert np.all((a2 >= 0) & (a2 <= 1))
+        xs.layer2 = (a2, *x.layer2[1:])
+        f = api.walk(api.Media.from_inputs(xs), o0)
+        torch.cuda.synchronize()
+        assert api.read_status(f["_workspace"])[0] in (0, 4)
+        Rs.append(f["R"].cpu().numpy())
+        a2s.append(a2.astype(np.float64))
+    fd = (Rs[1] - Rs[0]) / (a2s[1] - a2s[0])
+    err = np.abs(gs["d_alpha2"] - fd)
+    print("d R / d alpha2: max |score - central difference|", err.max(),
+          "max |fd|", np.abs(fd).max())
+    assert np.all(err <= 2e-3 * np.abs(fd) + 1e-4)
+
+
 def test_alpha_gradient_equals_crn_finite_difference(api):
     # Roulette off: path geometry does not depend on alpha, so the forward
     # estimate is a polynomial in alpha and the replay gives its derivative.
