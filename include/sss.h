@@ -295,8 +295,15 @@ sss_status sss_walk_bwd(const sss_params* p, const sss_walk_opts* o, void* works
 
 /* Waits for `stream`, then returns the status word the last call that used
  * `workspace` left (SSS_FLAG_* bits) in *flags and maps it to a status:
- * SSS_ERR_DEVICE_PARAM, SSS_ERR_OVERFLOW, SSS_ERR_STEP_LIMIT or SSS_OK. */
+ * SSS_ERR_TIMEOUT, SSS_ERR_DEVICE_PARAM, SSS_ERR_OVERFLOW, SSS_ERR_STEP_LIMIT
+ * or SSS_OK (in that order of precedence). */
 sss_status sss_read_status(const void* workspace, sss_stream_t stream, uint32_t* flags);
+
+/* The same for the workspace of the last successful sss_walk, sss_walk_bwd,
+ * sss_walk_noalloc or sss_decode call enqueued on `stream` (the library
+ * remembers one per stream; thread-safe).  SSS_ERR_INVALID_ARG if no such
+ * call was made on the stream or `flags` is NULL. */
+sss_status sss_last_device_status(sss_stream_t stream, uint32_t* flags);
 
 /* Philox4x32-10 blocks computed by the device code the walk uses
  * (diagnostic): out[4*i .. 4*i+3] = Philox(ctr[4*i .. 4*i+3], key).

@@ -97,6 +97,8 @@ def _load():
     lib.sss_probe.restype = C.c_int
     lib.sss_probe_ops_per_thread_iter.argtypes = [C.c_int32]
     lib.sss_probe_ops_per_thread_iter.restype = C.c_int64
+    lib.sss_last_device_status.argtypes = [C.c_void_p, C.POINTER(C.c_uint32)]
+    lib.sss_last_device_status.restype = C.c_int
     lib.sss_selftest_bounded_wait.argtypes = [C.c_void_p, C.c_int64, C.c_void_p]
     lib.sss_selftest_bounded_wait.restype = C.c_int
     lib.sss_abi_version.argtypes = []
@@ -300,6 +302,14 @@ def read_status(workspace: torch.Tensor, stream=None):
     """(status code, flag bits) left in the workspace by the last call."""
     flags = C.c_uint32(0)
     code = lib.sss_read_status(_ptr(workspace), _stream(stream), C.byref(flags))
+    return code, flags.value
+
+
+def last_device_status(stream=None):
+    """(status code, flag bits) of the last walk, adjoint or decode call
+    enqueued on `stream` (sss_last_device_status; waits for the stream)."""
+    flags = C.c_uint32(0)
+    code = lib.sss_last_device_status(_stream(stream), C.byref(flags))
     return code, flags.value
 
 

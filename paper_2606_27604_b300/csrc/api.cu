@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/sss.h"
+#include "last_status.cuh"
 #include "walk_kernels.cuh"
 
 using namespace sss;
@@ -184,6 +185,7 @@ thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
 
 // Graph cache: one instantiated graph per exact argument set.
 std::map<std::string, cudaGraphExec_t> g_graphs;
+std::map<cudaStream_t, const void*> g_last_ws;  // guarded by g_mu
 
 template <class T>
 void put(std::string& k, const T& v) {
@@ -343,9 +345,21 @@ sss_status enqueue_walk(bool adj, const sss_params* p, const sss_walk_opts* o, v
   return cudaGetLastError() == cudaSuccess ? SSS_OK : SSS_ERR_CUDA;
 }
 
+sss_status run_impl(bool adj, const sss_params* p, const sss_walk_opts* o, void* ws, size_t wsb,
+                    sss_tallies* out, const sss_grad_in* gin, sss_grad_out* gout,
+                    sss_stream_t stream);
+
 sss_status run(bool adj, const sss_params* p, const sss_walk_opts* o, void* ws, size_t wsb,
                sss_tallies* out, const sss_grad_in* gin, sss_grad_out* gout,
                sss_stream_t stream) {
+  const sss_status r = run_impl(adj, p, o, ws, wsb, out, gin, gout, stream);
+  if (r == SSS_OK) note_last_workspace(static_cast<cudaStream_t>(stream), ws);
+  return r;
+}
+
+sss_status run_impl(bool adj, const sss_params* p, const sss_walk_opts* o, void* ws, size_t wsb,
+                    sss_tallies* out, const sss_grad_in* gin, sss_grad_out* gout,
+                    sss_stream_t stream) {
   if (!params_ok(p) || !opts_ok(o)) return SSS_ERR_INVALID_ARG;
   if ((uint64_t)o->instance_offset + (uint64_t)p->n_inst > 0x100000000ull)
     return SSS_ERR_INVALID_ARG;
@@ -470,6 +484,13 @@ sss_status sss_read_status(const void* workspace, sss_stream_t stream, uint32_t*
   return SSS_OK;
 }
 
+sss_status sss_last_device_status(sss_stream_t stream, uint32_t* flags) {
+  if (!flags) return SSS_ERR_INVALID_ARG;
+  const void* ws = last_workspace(static_cast<cudaStream_t>(stream));
+  if (!ws) return SSS_ERR_INVALID_ARG;
+  return sss_read_status(ws, stream, flags);
+}
+
 sss_status sss_philox(const uint32_t* ctr, uint64_t key, int64_t n, uint32_t* out,
                       sss_stream_t stream) {
   if (n < 0 || (n > 0 && (!ctr || !out))) return SSS_ERR_INVALID_ARG;
@@ -510,3 +531,15 @@ const char* sss_status_string(sss_status s) {
 int32_t sss_abi_version(void) { return SSS_ABI_VERSION; }
 
 }  // extern "C"
+
+namespace sss {
+void note_last_workspace(cudaStream_t stream, const void* workspace) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_last_ws[stream] = workspace;
+}
+const void* last_workspace(cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_last_ws.find(stream);
+  return it == g_last_ws.end() ? nullptr : it->second;
+}
+}  // namespace sss

@@ -12,6 +12,7 @@
 
 #include "../../include/sss.h"
 #include "decode_kernels.cuh"
+#include "last_status.cuh"
 
 using namespace sss::dec;
 
@@ -163,9 +164,22 @@ sss_status sss_selftest_bounded_wait(uint32_t* status, int64_t limit_cycles,
              : SSS_ERR_CUDA;
 }
 
+static sss_status decode_impl(const float* rgb, int64_t T, const void* packed, void* workspace,
+                              size_t workspace_bytes, float* alpha, float* g, float* sigma_t,
+                              float* w, sss_stream_t stream);
+
 sss_status sss_decode(const float* rgb, int64_t T, const void* packed, void* workspace,
                       size_t workspace_bytes, float* alpha, float* g, float* sigma_t, float* w,
                       sss_stream_t stream) {
+  const sss_status r =
+      decode_impl(rgb, T, packed, workspace, workspace_bytes, alpha, g, sigma_t, w, stream);
+  if (r == SSS_OK) sss::note_last_workspace(static_cast<cudaStream_t>(stream), workspace);
+  return r;
+}
+
+static sss_status decode_impl(const float* rgb, int64_t T, const void* packed, void* workspace,
+                              size_t workspace_bytes, float* alpha, float* g, float* sigma_t,
+                              float* w, sss_stream_t stream) {
   if (T < 0 || T > ((int64_t)1 << 31) || !packed || !workspace) return SSS_ERR_INVALID_ARG;
   if (T > 0 && (!rgb || !alpha || !g || !sigma_t || !w)) return SSS_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)) ||

@@ -442,6 +442,24 @@ def test_three_identical_media_equal_one(api):
 
 
 # ----------------------------------------------------------------- edges --
+def test_last_device_status_follows_the_stream(api):
+    # sss_last_device_status reads the status word of the last call on the
+    # stream: a batch with an albedo outside [0, 1] flags SSS_FLAG_PARAM
+    # (SSS_ERR_DEVICE_PARAM), and a clean batch after it reads OK
+    import torch
+    x = inputs.spectral_field(n_texels=1, param_seed=2, n_paths=512)
+    bad = x.subset(np.arange(x.n_inst))
+    bad.alpha = bad.alpha.copy()
+    bad.alpha[0, 5] = 1.5
+    api.walk(api.Media.from_inputs(bad), opts(api, nbins=8))
+    code, flags = api.last_device_status()
+    assert code == 6 and flags & 0x1, (code, flags)
+    api.walk(api.Media.from_inputs(x), opts(api, nbins=8))
+    code, flags = api.last_device_status()
+    assert code == 0 and flags == 0, (code, flags)
+    torch.cuda.synchronize()
+
+
 def test_edge_cases(api):
     import torch
     # empty batch
