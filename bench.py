@@ -48,8 +48,8 @@ DECODER_MACS_PER_TEXEL = (3 * 256 + 256 * 256 + 256 * 5) + (5 * 512 + 512 * 512 
 # dram__bytes_write.sum) of the 1024-texel case, scaled by 64 to the
 # 65536-texel launch (the traffic grows with the instances walked).  Valid
 # only while the kernel sources are the ones captured (sha1 below).
-WALK_TRAFFIC = {"bytes_per_launch": (61.705216e6 + 11.656704e6) * 64,
-                "source_sha1": "679dd22c00a894eb1527185534349f180863cabd",
+WALK_TRAFFIC = {"bytes_per_launch": (61.667584e6 + 11.258880e6) * 64,
+                "source_sha1": "b9f67d5188db4df09ea3427ca0e8c234e44f3894",
                 "capture": "profiles/walk_persistent_spectral_field.md"}
 
 
