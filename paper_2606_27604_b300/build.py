@@ -9,7 +9,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsss.so")
 SOURCES = ["api.cu", "walk_kernels.cu", "decode.cu", "decode_api.cu", "noalloc.cu", "fit.cu",
            "probe.cu"]
-HEADERS = ["walk_core.cuh", "walk_kernels.cuh", "decode_kernels.cuh", "fit_kernels.cuh"]
+HEADERS = ["walk_core.cuh", "walk_kernels.cuh", "decode_kernels.cuh", "fit_kernels.cuh",
+           "hero.cuh", "last_status.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -77,39 +77,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// The same copy multicast to every CTA of the cluster in `mask`: the box
-// lands at the same shared-memory offset in each, and each destination's
-// mbarrier at the same offset receives the bytes.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y,
-                                               uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-// All threads of all CTAs of the cluster (release / acquire).
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
-               ::: "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -149,16 +116,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
-      : "memory");
-}
-
-// Arrives on the mbarrier at this offset in every CTA of `mask` once the
-// MMAs issued so far have completed.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster"
-      ".b64 [%0], %1;" ::"r"(smem_u32(bar)),
-      "h"(mask)
       : "memory");
 }
 
@@ -296,18 +253,12 @@ __device__ __forceinline__ void epi_final_group(const float* v, int row, int P,
 // issues the MMAs into one of two TMEM accumulators; warps 2..9 drain the
 // other accumulator (two warps per TMEM lane quarter, alternate 16-column
 // chunks), so a tile's epilogue overlaps the next tile's MMAs.  The bias
-// vector is staged once in shared memory.
-//
-// CM > 1: thread-block clusters of CM CTAs along M share the weight tile.
-// The CTAs of a cluster work on CM consecutive M tiles of the same N tile in
-// step; each loads 1/CM of every B k-block and multicasts it to all of
-// them, so B leaves L2 once per cluster instead of once per CTA.  A stage
-// is refilled only after every CTA's MMAs have read it: each MMA warp's
-// commit arrives on that stage's "empty" barrier in all CTAs (count CM).
+// vector is staged once in shared memory.  Every CTA loads its own A and B
+// tiles with its own TMA copies into its own shared memory.
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 
-template <int BN, int EPI, int CM>
+template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                  const __grid_constant__ CUtensorMap tmap_b, int a_x0, int num_kb,
@@ -317,13 +268,8 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
   constexpr int B_BYTES = BN * BK * 2;
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   constexpr int TCOLS = TmemCols<2 * BN>::value2;
-  constexpr int SLICE_ROWS = BN / CM;            // B rows each CTA of a cluster loads
-  constexpr int SLICE_BYTES = SLICE_ROWS * BK * 2;
-  constexpr uint16_t kMask = (uint16_t)((1u << CM) - 1u);
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
   static_assert(B_BYTES % 1024 == 0, "tiles must stay 1024-byte aligned");
-  static_assert(CM >= 1 && CM <= 8 && BN % CM == 0 && SLICE_BYTES % 1024 == 0,
-                "B slices must keep the 1024-byte swizzle atoms whole");
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -338,16 +284,14 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  // tiles of the cluster: CM consecutive M tiles x one N tile
-  const int crank = CM > 1 ? (int)cluster_ctarank() : 0;
-  const long long first = CM > 1 ? (long long)cluster_id_x() : (long long)blockIdx.x;
-  const long long step = CM > 1 ? (long long)cluster_count_x() : (long long)gridDim.x;
-  const long long total = ((m_tiles + CM - 1) / CM) * (long long)n_tiles;
+  const long long first = (long long)blockIdx.x;
+  const long long step = (long long)gridDim.x;
+  const long long total = m_tiles * (long long)n_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CM);  // one commit from each CTA of the cluster
+      mbar_init(&empty[s], 1);  // the MMA warp's commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -367,7 +311,6 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
   for (int j = threadIdx.x; j < n_tiles * BN; j += blockDim.x) sbias[j] = bias[j];
   tc_fence_before();
   __syncthreads();
-  if (CM > 1) cluster_sync();  // every CTA's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -379,7 +322,7 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                    : "memory");
       long long it = 0;
       for (long long t = first; t < total && !*abort_flag; t += step) {
-        const int m_tile = (int)((t / n_tiles) * CM + crank), n_tile = (int)(t % n_tiles);
+        const int m_tile = (int)(t / n_tiles), n_tile = (int)(t % n_tiles);
         for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = (int)(it % STAGES);
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -388,14 +331,10 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
             *abort_flag = 1u;
             break;
           }
-          mbar_expect_tx(&full[s], STAGE_BYTES);  // own A + every slice of B
+          mbar_expect_tx(&full[s], STAGE_BYTES);  // A tile + B tile
           uint8_t* sa = smem + s * STAGE_BYTES;
           tma_load_2d(sa, &tmap_a, a_x0 + kb * BK, m_tile * BM, &full[s]);
-          if (CM == 1)
-            tma_load_2d(sa + A_BYTES, &tmap_b, kb * BK, n_tile * BN, &full[s]);
-          else
-            tma_load_2d_mc(sa + A_BYTES + crank * SLICE_BYTES, &tmap_b, kb * BK,
-                           n_tile * BN + crank * SLICE_ROWS, &full[s], kMask);
+          tma_load_2d(sa + A_BYTES, &tmap_b, kb * BK, n_tile * BN, &full[s]);
         }
       }
     }
@@ -427,9 +366,8 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)  // K = 16 per MMA: advance 32 bytes
             umma_bf16(acc, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
-          // frees the stage (in every CTA of the cluster) once these MMAs have read it
-          if (CM == 1) umma_commit(&empty[s]);
-          else umma_commit_mc(&empty[s], kMask);
+          // frees the stage once these MMAs have read it
+          umma_commit(&empty[s]);
         }
         umma_commit(&tfull[b]);    // accumulator b complete
       }
@@ -440,7 +378,7 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
     const int half = (warp - 2) >> 2;  // which alternate column chunks
     int i = 0;
     for (long long t = first; t < total; t += step, ++i) {
-      const int m_tile = (int)((t / n_tiles) * CM + crank), n_tile = (int)(t % n_tiles);
+      const int m_tile = (int)(t / n_tiles), n_tile = (int)(t % n_tiles);
       const int b = i & 1;
       const bool ok = mbar_wait(&tfull[b], (uint32_t)(i >> 1) & 1u);
       if (!ok) {
@@ -492,8 +430,6 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
   }
   tc_fence_before();
   __syncthreads();
-  // no CTA leaves while another may still signal its barriers
-  if (CM > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -575,7 +511,7 @@ cudaError_t launch_bounded_wait_selftest(unsigned int* status, long long limit, 
 }
 
 // ---------------------------------------------------------------- launch --
-template <int BN, int EPI, int CM>
+template <int BN, int EPI>
 static cudaError_t launch_gemm_t(const CUtensorMap& ta, const CUtensorMap& tb, int a_x0,
                                  int num_kb, int n_tiles, long long m_tiles, const float* bias,
                                  const EpiParams& ep, unsigned int* status, cudaStream_t st) {
@@ -584,58 +520,32 @@ static cudaError_t launch_gemm_t(const CUtensorMap& ta, const CUtensorMap& tb, i
   constexpr size_t ring = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2);
   const size_t smem = (ring > 120 * 1024 ? ring : 120 * 1024) + 1024 + 256 +
                       (size_t)n_tiles * BN * sizeof(float);
-  auto fn = gemm_bf16_kernel<BN, EPI, CM>;
+  auto fn = gemm_bf16_kernel<BN, EPI>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long total = (long long)n_tiles * ((m_tiles + CM - 1) / CM);  // cluster tiles
+  const long long total = (long long)n_tiles * m_tiles;
   if (total == 0) return cudaSuccess;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  long long slots = sms;  // resident CTAs
-  if (CM > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CM;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3((unsigned)(sms / CM * CM));
-    int clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
-    if (e != cudaSuccess) return e;
-    if (clusters < 1) return cudaErrorInvalidConfiguration;
-    slots = (long long)clusters * CM;
-  }
-  const long long ctas = (total < slots / CM ? total : slots / CM) * CM;
-  cfg.gridDim = dim3((unsigned)ctas);
-  return cudaLaunchKernelEx(&cfg, fn, ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status);
+  // persistent: one CTA per SM (its shared memory allows no second one)
+  const long long ctas = total < sms ? total : sms;
+  fn<<<(unsigned)ctas, kThreads, smem, st>>>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep,
+                                             status);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_gemm(int bn, int epi, int cm, const CUtensorMap& ta, const CUtensorMap& tb,
+cudaError_t launch_gemm(int bn, int epi, const CUtensorMap& ta, const CUtensorMap& tb,
                         int a_x0, int num_kb, int n_tiles, long long m_tiles, const float* bias,
                         const EpiParams& ep, unsigned int* status, cudaStream_t st) {
-#define SSS_GEMM(BN_, EPI_, CM_) \
-  return launch_gemm_t<BN_, EPI_, CM_>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st)
-  if (epi == EPI_FINAL && bn == 144) {
-    if (cm == 2) SSS_GEMM(144, EPI_FINAL, 2);
-    SSS_GEMM(144, EPI_FINAL, 1);
-  }
+#define SSS_GEMM(BN_, EPI_) \
+  return launch_gemm_t<BN_, EPI_>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st)
+  if (epi == EPI_FINAL && bn == 144) SSS_GEMM(144, EPI_FINAL);
   if (epi == EPI_HIDDEN) {
     switch (bn) {
-      case 16: SSS_GEMM(16, EPI_HIDDEN, 1);
-      case 128:
-        if (cm == 2) SSS_GEMM(128, EPI_HIDDEN, 2);
-        SSS_GEMM(128, EPI_HIDDEN, 1);
-      case 256:
-        if (cm == 4) SSS_GEMM(256, EPI_HIDDEN, 4);
-        if (cm == 2) SSS_GEMM(256, EPI_HIDDEN, 2);
-        SSS_GEMM(256, EPI_HIDDEN, 1);
+      case 16: SSS_GEMM(16, EPI_HIDDEN);
+      case 128: SSS_GEMM(128, EPI_HIDDEN);
+      case 256: SSS_GEMM(256, EPI_HIDDEN);
     }
   }
 #undef SSS_GEMM

@@ -213,12 +213,6 @@ static sss_status decode_impl(const float* rgb, int64_t T, const void* packed, v
     const __nv_bfloat16* a; int a_cols; int a_x0; int layer; int bn; int epi;
     __nv_bfloat16* out; int ldc; int col0; int n_valid; int act;
   };
-  // CTAs per cluster along M sharing each weight tile by multicast, per
-  // tile width (see gemm_bf16_kernel)
-  auto cluster_m = [](int bn, int epi) {
-    if (epi == EPI_FINAL) return kClusterFinal;
-    return bn == 256 ? kCluster256 : bn == 128 ? kCluster128 : 1;
-  };
   // enc1..dec_t2: hidden layers; dec_t3: the parameter epilogue.
   // X0 is [T][256] in BUF_R1 (row pitch 256), X1 likewise in BUF_R2.
   const Step steps[9] = {
@@ -235,9 +229,8 @@ static sss_status decode_impl(const float* rgb, int64_t T, const void* packed, v
   for (const Step& s : steps) {
     const LayerSpec& L = kLayers[s.layer];
     CUtensorMap ta, tb;
-    const int cm = cluster_m(s.bn, s.epi);
     if (!make_map(&ta, s.a, (uint64_t)T, (uint64_t)s.a_cols, 128) ||
-        !make_map(&tb, W(s.layer), (uint64_t)L.rows, (uint64_t)L.cols, (uint32_t)(s.bn / cm)))
+        !make_map(&tb, W(s.layer), (uint64_t)L.rows, (uint64_t)L.cols, (uint32_t)s.bn))
       return SSS_ERR_CUDA;
     EpiParams ep{};
     ep.out = s.out;
@@ -255,7 +248,7 @@ static sss_status decode_impl(const float* rgb, int64_t T, const void* packed, v
     ep.M = T;
     const int num_kb = (L.cols + 63) / 64;
     const int n_tiles = L.rows / s.bn;
-    if (launch_gemm(s.bn, s.epi, cm, ta, tb, s.a_x0, num_kb, n_tiles, mt, B(s.layer), ep, status,
+    if (launch_gemm(s.bn, s.epi, ta, tb, s.a_x0, num_kb, n_tiles, mt, B(s.layer), ep, status,
                     st) != cudaSuccess)
       return SSS_ERR_CUDA;
   }

@@ -22,11 +22,6 @@ enum : unsigned int { DEC_FLAG_TIMEOUT = 0x10u };
 constexpr int kDstBands = 81;
 constexpr int kPairs = 41;
 constexpr int kFinalBN = 144;
-// CTAs per thread-block cluster along M that share each weight tile through
-// TMA multicast, by layer kind (1 = no cluster).
-constexpr int kCluster256 = 2;
-constexpr int kCluster128 = 2;
-constexpr int kClusterFinal = 2;
 constexpr int kFinalRows = 11 * kFinalBN;  // 1584
 
 __host__ __device__ inline int dect_out_source_row(int r) {
@@ -50,7 +45,7 @@ struct EpiParams {
 
 cudaError_t launch_bounded_wait_selftest(unsigned int* status, long long limit,
                                          cudaStream_t st);
-cudaError_t launch_gemm(int bn, int epi, int cm, const CUtensorMap& ta, const CUtensorMap& tb,
+cudaError_t launch_gemm(int bn, int epi, const CUtensorMap& ta, const CUtensorMap& tb,
                         int a_x0, int num_kb, int n_tiles, long long m_tiles, const float* bias,
                         const EpiParams& ep, unsigned int* status, cudaStream_t st);
 cudaError_t launch_enc0(const float* rgb, long long T, const __nv_bfloat16* W, const float* b,
