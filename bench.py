@@ -9,9 +9,15 @@ adjoint/forward time ratio on the adjoint workload (64 x 64 x 81 at 2^16
 paths), the ALU roofline of the walk kernel and the FP64 oracle timed on the
 host cores on a sample of the same workload.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
-Under torchrun (N > 1) every rank walks its own field of the same size
-(weak scaling, no collective on the data path).
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference] [--strong]
+Under torchrun (N > 1) the batch is sharded by contiguous instance ranges
+(instance_offset = the range's first global instance), so every path keeps
+its random numbers whatever the rank count:
+  * default (weak scaling): rank r walks its own full-size field as
+    instances r*n .. r*n + n - 1 of a global batch of N fields; there is no
+    collective on the data path;
+  * --strong: one field is cut into N ranges and every step ends with one
+    all_gather of R and the radial bins (the only exchange the walk has).
 """
 import argparse
 import json
@@ -49,8 +55,7 @@ DECODER_MACS_PER_TEXEL = (3 * 256 + 256 * 256 + 256 * 5) + (5 * 512 + 512 * 512 
 # 65536-texel launch (the traffic grows with the instances walked).  Valid
 # only while the kernel sources are the ones captured (sha1 below).
 WALK_TRAFFIC = {"bytes_per_launch": (61.667584e6 + 11.258880e6) * 64,
-                "source_sha1": "b9f67d5188db4df09ea3427ca0e8c234e44f3894",
-                "capture": "profiles/walk_persistent_spectral_field.md"}
+                "source_sha1": "b9f67d5188db4df09ea3427ca0e8c234e44f3894"}
 
 
 def _walk_source_sha1():
@@ -175,16 +180,18 @@ def cpu_baseline_sample(n_texels=24):
             "other_configs": per_config}
 
 
-def run_pipeline(args):
-    """RGB texture -> decoder -> walk, timed end to end on the GPU, with the
-    error against the FP64 oracle pipeline on a 32 x 32 texel subset."""
+def pipeline_leg(side=1024, oracle_block=32, dev_index=0):
+    """RGB texture -> decoder (tensor cores) -> batched walk at 1024 paths per
+    texel and band (the full-pipeline workload), timed on the GPU, with the
+    error of R against the FP64 oracle pipeline (oracle decoder + oracle
+    walk, same Philox streams) on a 32 x 32 texel block and that oracle
+    pipeline timed on the host cores."""
     import torch
     import oracle
     from oracle import decoder as dec_ref
     from paper_2606_27604_b300 import api, inputs
-    side = args.pipeline_side
     T = side * side
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", dev_index)
     rgb_np = inputs.rgb_texture(side=side, seed=4)
     W = inputs.decoder_weights(seed=4)
     rgb = torch.from_numpy(rgb_np).to(dev)
@@ -195,14 +202,12 @@ def run_pipeline(args):
     o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=1004)
     m = api.Media(prm["alpha"], prm["sigma_t"], prm["g"], prm["w"], None, 1024, None, 1.4)
     wsp = api.alloc_workspace(m, o)
-    out = api.alloc_tallies(m, o)
+    # only the outputs the comparison reads (the full set would add ~90 GB)
+    d = lambda: torch.empty(m.n_inst, dtype=torch.float64, device=dev)
+    out = {"R": d(), "stderr_R": d(), "steps": d()}
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        api.decode(rgb, packed, workspace=dws, out=prm)
-        api.walk(m, o, workspace=wsp, out=out)
-
-    step()
+    api.decode(rgb, packed, workspace=dws, out=prm)      # warm-up
+    api.walk(m, o, workspace=wsp, out=out)
     torch.cuda.synchronize()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e[0].record(stream)
@@ -212,33 +217,47 @@ def run_pipeline(args):
     e[2].record(stream)
     torch.cuda.synchronize()
     t_dec, t_walk = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
-    # oracle pipeline on the first 32 x 32 texels (rows of the texture)
-    sub = 32 * 32
+    dcode, _ = api.read_status(dws)
+    wcode, _ = api.read_status(wsp)
+    # oracle pipeline on a 32 x 32 block of texels (rows 0..31, columns 0..31)
+    blk = (np.arange(oracle_block)[:, None] * side + np.arange(oracle_block)[None, :]).ravel()
+    sub = len(blk)
     t_or = time.perf_counter()
-    ref = dec_ref.decode(rgb_np[:sub], W, bf16_activations=True)
-    Tb = sub
-    ids = (np.arange(81)[:, None] * T + np.arange(sub)[None, :]).reshape(-1)
+    ref = dec_ref.decode(rgb_np[blk], W, bf16_activations=True)
+    ids = (np.arange(81)[:, None] * T + blk[None, :]).reshape(-1)   # band-major numbers
     refw = oracle.walk(ref["alpha"].astype(np.float32), ref["sigma_t"].astype(np.float32),
                        ref["g"].astype(np.float32), ref["w"].astype(np.float32),
-                       np.full(81 * Tb, 1024, np.uint32), None, 1.4,
+                       np.full(81 * sub, 1024, np.uint32), None, 1.4,
                        oracle.OracleOpts(nbins=64, r_max_mm=10.0, seed=1004), inst_ids=ids)
     t_or = time.perf_counter() - t_or
-    R = out["R"].cpu().numpy()[ids]
-    se = np.sqrt(refw["se_R"] ** 2 + out["stderr_R"].cpu().numpy()[ids] ** 2)
+    ii = torch.from_numpy(ids).to(dev)
+    R = out["R"][ii].cpu().numpy()
+    se = np.sqrt(refw["se_R"] ** 2 + out["stderr_R"][ii].cpu().numpy() ** 2)
     z = (R - refw["R"]) / np.maximum(se, 1e-12)
     paths = 81.0 * T * 1024
-    line = {"metric": "full pipeline RGB -> decoder -> walk", "workload":
-            f"{side}x{side} RGB, 81 bands, 1024 paths, 64 bins, n=1.4",
-            "decode_ms": t_dec * 1e3, "walk_ms": t_walk * 1e3,
-            "total_ms": (t_dec + t_walk) * 1e3, "paths_per_s": paths / (t_dec + t_walk),
-            "subset": "32x32 texels x 81 bands vs FP64 oracle decoder + oracle walk",
-            "R_z_abs_max": float(np.abs(z).max()), "R_z_rms": float(np.sqrt((z ** 2).mean())),
-            "R_rel_err_median": float(np.median(np.abs(R - refw["R"]) / refw["R"])),
-            "frac_within_4sigma": float((np.abs(z) <= 4).mean()),
-            "cpu_baseline": {"value": 81.0 * sub * 1024 / t_or, "unit": "paths/s",
-                             "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"the 32x32-texel subset: FP64 decoder and walk, "
-                                       f"{81 * sub * 1024} paths, {t_or:.1f} s"}}
+    res = {"workload": f"{side}x{side} RGB -> decoder -> 81 bands x 1024 paths, 64 bins, n=1.4",
+           "decode_ms": t_dec * 1e3, "walk_ms": t_walk * 1e3,
+           "total_ms": (t_dec + t_walk) * 1e3, "paths_per_s": paths / (t_dec + t_walk),
+           "steps_per_path": float(out["steps"].mean().item()),
+           "status": [dcode, wcode],
+           "subset": f"{oracle_block}x{oracle_block} texel block x 81 bands vs the FP64 oracle "
+                     "decoder + oracle walk on the same Philox streams",
+           "R_rel_err_median": float(np.median(np.abs(R - refw["R"]) / refw["R"])),
+           "R_z_abs_max": float(np.abs(z).max()), "R_z_rms": float(np.sqrt((z ** 2).mean())),
+           "frac_within_4sigma": float((np.abs(z) <= 4).mean()),
+           "cpu_baseline": {"value": 81.0 * sub * 1024 / t_or, "unit": "paths/s",
+                            "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"the {oracle_block}x{oracle_block} block: FP64 decoder "
+                                      f"and walk, {81 * sub * 1024} paths, {t_or:.1f} s"}}
+    del wsp, out, prm, dws
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_pipeline(args):
+    """The full pipeline alone, as one JSON line."""
+    line = dict(metric="full pipeline RGB -> decoder -> walk",
+                **pipeline_leg(side=args.pipeline_side))
     print(json.dumps(line), flush=True)
     return 0
 
@@ -350,7 +369,9 @@ def main():
     ap.add_argument("--no-probe", action="store_true",
                     help="skip the issue-rate probes")
     ap.add_argument("--pipeline", action="store_true",
-                    help="run the full RGB -> decoder -> walk pipeline instead")
+                    help="run the full RGB -> decoder -> walk pipeline alone")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="skip the full-pipeline leg of the default line")
     ap.add_argument("--pipeline-side", type=int, default=1024)
     ap.add_argument("--lut", action="store_true", help="time the LUT precompute instead")
     ap.add_argument("--lut-side", type=int, default=128)
@@ -362,6 +383,9 @@ def main():
                     help="pick the walk kernel's launch shape with the autotuner first")
     ap.add_argument("--texels", type=int, default=WORKLOAD["texels"],
                     help="texels of the spectral field (smaller values: profiling cases)")
+    ap.add_argument("--strong", action="store_true",
+                    help="N > 1: shard one field across the ranks and gather R and the bins "
+                         "every step (strong scaling) instead of one field per rank")
     args = ap.parse_args()
     if args.texels != WORKLOAD["texels"]:
         WORKLOAD["texels"] = args.texels
@@ -386,11 +410,23 @@ def main():
         dist = None
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
-    from paper_2606_27604_b300 import api
+    from paper_2606_27604_b300 import api, shard
 
-    x = spectral_inputs(rank)
+    strong = ws > 1 and args.strong
+    if strong:
+        # one field, contiguous instance ranges, one gather per step
+        x_all = spectral_inputs(0)
+        x, begin = shard.shard_batch(x_all, rank, ws)
+        n_total = x_all.n_inst
+        del x_all
+    else:
+        # rank r's field is instances r*n .. r*n + n - 1 of the global batch
+        x = spectral_inputs(rank)
+        begin = rank * x.n_inst
+        n_total = x.n_inst * ws
     m = api.Media.from_inputs(x, device=dev)
-    o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=WORKLOAD["walk_seed"] + 7919 * rank)
+    o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=WORKLOAD["walk_seed"],
+                        instance_offset=begin)
     if args.autotune:
         from paper_2606_27604_b300 import autotune
         o = autotune.tune(m, o)
@@ -403,6 +439,14 @@ def main():
     def barrier():
         if dist is not None:
             dist.barrier()
+
+    def gpu_walk(_x, _begin):
+        api.walk(m, o, workspace=wsp, out=out)
+        return out["R"], out["bins"]
+
+    def step():
+        # the walk, then (strong sharding) the one exchange: R and the bins
+        shard.walk_and_gather(gpu_walk, x, begin, n_total, gather=strong)
 
     for _ in range(args.warmup):
         api.walk(m, o, workspace=wsp, out=out)
@@ -424,7 +468,7 @@ def main():
     t0.record(stream)
     for i in range(args.steps):
         api.profile_events(k_start[i], k_stop[i])
-        api.walk(m, o, workspace=wsp, out=out)
+        step()
     api.profile_events(None, None)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -436,7 +480,9 @@ def main():
         tt = torch.tensor([elapsed], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         elapsed = float(tt.item())
-    total_paths = paths_per_step * args.steps * ws
+    # units all ranks processed: each rank's paths (equal shares up to one instance)
+    total_paths = (n_total * WORKLOAD["paths_per_instance"] if strong
+                   else paths_per_step * ws) * args.steps
     value = total_paths / elapsed
     steps_mean = float(out["steps"].mean().item())
     total_draws = float(out["steps"].double().sum().item()) * WORKLOAD["paths_per_instance"]
@@ -593,7 +639,7 @@ def main():
 
     # ---- decoder (RGB -> per-band mixture parameters, tensor cores) --------
     decoder = None
-    if not args.no_decoder:
+    if not args.no_decoder and ws == 1:
         from paper_2606_27604_b300 import inputs
         side = 1024
         rgb = torch.from_numpy(inputs.rgb_texture(side=side, seed=4)).to(dev)
@@ -623,6 +669,11 @@ def main():
                    "frac": flops / (dms / 1e3) / 1e12 / peak_bf16[0],
                    "flops_per_texel": 2 * DECODER_MACS_PER_TEXEL, "status": dcode}
         del dws, dout
+
+    # ---- full pipeline: RGB -> decoder -> walk (one GPU) -------------------
+    pipeline = None
+    if not args.no_pipeline and ws == 1:
+        pipeline = pipeline_leg(side=args.pipeline_side)
 
     # ---- roofline of the walk kernel --------------------------------------
     kmean = float(np.mean(kern))
@@ -670,9 +721,12 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": dict(WORKLOAD, parallelism=f"replicas{ws}",
+            "higher_is_better": True, "scaling": "strong" if strong else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(WORKLOAD,
+                           parallelism=(f"instance-shard x{ws}, one field, all_gather per step"
+                                        if strong else
+                                        f"instance-shard x{ws}, one field per rank"),
                            l2=f"inputs ({x.alpha.nbytes * 4 / 1e6:.0f} MB) and tally workspace "
                               f"({wsp_bytes / 1e9:.1f} GB) vs the 126 MB L2",
                            steps_per_path=steps_mean),
@@ -680,7 +734,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu,
             "adjoint_forward_ratio": ratio, "baselines": baselines, "hero_wavelength": hero,
             "probe": probe,
-            "decoder": decoder,
+            "decoder": decoder, "pipeline": pipeline,
             "launch_shape": {k: getattr(o, k) for k in ("block_threads", "unit_paths", "regroup")},
             "status_flags": flags}
     if rank == 0:

@@ -18,7 +18,8 @@
  *    device memory: the caller owns every buffer, including the workspace.
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *    stream) and runs asynchronously: results are valid once the stream has
- *    reached the call's end.
+ *    reached the call's end.  (Exceptions, each stated where it applies:
+ *    the status reads, and the plain schedule with per-instance budgets.)
  *  - Errors a host can see (NULL pointer where one is required, sizes out of
  *    range, misaligned pointers, too small workspace) are returned at once
  *    and nothing is enqueued.  Errors only the device can see (invalid
@@ -39,7 +40,7 @@
 extern "C" {
 #endif
 
-#define SSS_ABI_VERSION 2
+#define SSS_ABI_VERSION 3
 #define SSS_KMAX 4          /* media per mixture supported (the paper uses 3) */
 #define SSS_NBINS_MAX 1024  /* radial bins supported */
 
@@ -120,9 +121,15 @@ typedef struct {
  *   want_sumsq      : 1 = also tally squared exit weights (standard errors).
  *   schedule        : 0 = persistent batched kernel over all instances;
  *                     1 = plain baseline, one launch per instance, one thread
- *                     per path, no regrouping.
+ *                     per path, no regrouping.  With per-instance budgets
+ *                     (n_paths non-NULL) the plain baseline is the one
+ *                     synchronous case: sss_walk copies the budgets to the
+ *                     host and waits for `stream` before it launches (each
+ *                     launch's grid depends on its budget), and it cannot be
+ *                     graph-captured (use_graph = 1: SSS_ERR_INVALID_ARG).
  *   use_graph       : 1 = capture the call's launches once in a CUDA graph
- *                     (cached per argument set) and replay it.
+ *                     (cached per argument set, at most 64 plans, the oldest
+ *                     dropped first) and replay it.
  *   block_threads, unit_paths, regroup : launch shape of the persistent
  *                     kernel (0 = built-in defaults); results do not depend
  *                     on them.
@@ -211,7 +218,12 @@ typedef struct {
  *                      fixed-point sums (weight * 2^32) in the order
  *                      bins, overflow, R_k, R1, T, A, then the plain counts
  *                      truncated and steps, then [sumsq bins, sumsq overflow]
- *                      (squared weights * 2^32). */
+ *                      (squared weights * 2^32).
+ *   profile [n_inst][nbins]  the normalised radial profile P_d(r) of Eq. 3
+ *                      (R_d(r) = R * P_d(r)): bins / R, the fraction of R
+ *                      leaving through each annulus; 0 where R = 0.  The
+ *                      scale-free tables of Sec. 4.2 are this profile at
+ *                      sigma_t = 1. */
 typedef struct {
   double* R;
   double* T;
@@ -225,6 +237,7 @@ typedef struct {
   uint64_t* truncated;
   double* steps;
   uint64_t* raw;
+  double* profile;
 } sss_tallies;
 
 /* Upstream derivatives d(loss)/d(tally) for sss_walk_bwd; float64 device,
@@ -426,8 +439,9 @@ void sss_profile_events(void* start, void* stop);
  *    sss_walk_workspace_size exceeds it return SSS_ERR_TOO_LARGE (at 64 bins,
  *    K = 3 and standard errors that is about 15,000 instances);
  *  - the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture on that device;
+ *    (cudaGetSymbolAddress) with that device current, and so does the first
+ *    call after the device's context has changed (cudaDeviceReset); make
+ *    those calls before any stream capture on that device;
  *  - every call shares the one array, which keeps the last call's contents:
  *    each call clears what must start at zero, but calls that overlap on
  *    the GPU (other streams, other threads) race and must be serialised;
@@ -456,13 +470,16 @@ enum {
   SSS_PROBE_FFMA2 = 1,  /* paired binary32 fused multiply-add (two lanes' ops) */
   SSS_PROBE_IMAD = 2,   /* 32-bit integer multiply-add                        */
   SSS_PROBE_LOP3 = 3,   /* 32-bit three-input logic operation                 */
-  SSS_PROBE_MUFU = 4    /* special-function unit (lg2.approx)                 */
+  SSS_PROBE_MUFU = 4,   /* special-function unit (lg2.approx)                 */
+  SSS_PROBE_PHILOX = 5  /* whole Philox4x32-10 blocks, as the walk draws them  */
 };
 
 /* Launches `blocks` blocks of 256 threads on `stream`, each thread running
- * `iters` iterations of eight independent chains of the probed operation,
- * and writes one float per thread to sink[blocks * 256] (device, caller
- * owned) so nothing is optimised away.  Asynchronous: time it with events
+ * `iters` iterations of eight independent chains of the probed operation
+ * (four chains of whole blocks for SSS_PROBE_PHILOX, each block's output
+ * the next block's counter, round keys in the kernel's parameter bank as
+ * the walk holds them), and writes one float per thread to sink[blocks *
+ * 256] (device, caller owned) so nothing is optimised away.  Asynchronous: time it with events
  * on the stream.  Operations executed = blocks * 256 * iters *
  * sss_probe_ops_per_thread_iter(kind).  Errors: SSS_ERR_INVALID_ARG for a
  * bad kind, iters < 1, blocks < 1 or a null sink; SSS_ERR_CUDA if the

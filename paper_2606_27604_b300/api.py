@@ -49,10 +49,12 @@ class Opts(C.Structure):
                 ("hero_texel_bands", C.c_int32), ("hero_orbits", C.c_int32)]
 
 
+TALLY_KEYS = ("R", "T", "A", "bins", "overflow", "R_k", "R1", "stderr_R", "stderr_bins",
+              "truncated", "steps", "raw", "profile")
+
+
 class Tallies(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("R", "T", "A", "bins", "overflow", "R_k", "R1",
-                                          "stderr_R", "stderr_bins", "truncated", "steps",
-                                          "raw")]
+    _fields_ = [(n, C.c_void_p) for n in TALLY_KEYS]
 
 
 class GradIn(C.Structure):
@@ -109,7 +111,7 @@ def _load():
     return lib
 
 
-ABI_VERSION = 2  # struct layouts below match this version of the C header
+ABI_VERSION = 3  # struct layouts below match this version of the C header
 
 lib = _load()
 
@@ -261,9 +263,7 @@ def walk(m: Media, o: WalkOptions, workspace: Optional[torch.Tensor] = None,
         workspace = alloc_workspace(m, o)
     if out is None:
         out = alloc_tallies(m, o, raw)
-    t = Tallies(**{k: _ptr(out.get(k)) for k in
-                   ("R", "T", "A", "bins", "overflow", "R_k", "R1", "stderr_R",
-                    "stderr_bins", "truncated", "steps", "raw")})
+    t = Tallies(**{k: _ptr(out.get(k)) for k in TALLY_KEYS})
     p, oc = m.c(), o.c()
     _check(lib.sss_walk(C.byref(p), C.byref(oc), _ptr(workspace), workspace.numel(),
                         C.byref(t), _stream(stream)), "sss_walk")
@@ -435,19 +435,19 @@ lib.sss_walk_noalloc.argtypes = [C.POINTER(Params), C.POINTER(Opts), C.POINTER(T
 lib.sss_walk_noalloc.restype = C.c_int
 
 
-def walk_noalloc(m: Media, o: WalkOptions, out: dict, stream=None):
+def walk_noalloc(m: Media, o: WalkOptions, out: dict, stream=None, read_flags: bool = True):
     """sss_walk_noalloc: the forward walk with the library's built-in scratch
     (for callers that cannot allocate device memory).  `out` must already
-    hold the output tensors (alloc_tallies); returns (status, flags) after
-    waiting for the stream."""
-    t = Tallies(**{k: _ptr(out.get(k)) for k in
-                   ("R", "T", "A", "bins", "overflow", "R_k", "R1", "stderr_R",
-                    "stderr_bins", "truncated", "steps", "raw")})
+    hold the output tensors (alloc_tallies).  With read_flags the call waits
+    for the stream and returns (status, device flags); without, it passes no
+    flag word, returns (status of the enqueue, None) at once, and the device
+    status can be read later with last_device_status."""
+    t = Tallies(**{k: _ptr(out.get(k)) for k in TALLY_KEYS})
     p, oc = m.c(), o.c()
     flags = C.c_uint32(0)
-    code = lib.sss_walk_noalloc(C.byref(p), C.byref(oc), C.byref(t), C.byref(flags),
-                                _stream(stream))
-    return code, flags.value
+    code = lib.sss_walk_noalloc(C.byref(p), C.byref(oc), C.byref(t),
+                                C.byref(flags) if read_flags else None, _stream(stream))
+    return code, (flags.value if read_flags else None)
 
 
 # --------------------------------------------------------------- LUT fit --
@@ -488,7 +488,7 @@ def lut_fit(R_lut, p_lut, a0, da, g0, dg, drho, r_mm, P_mc, R_mc, raw, K=3, step
     return loss, grad
 
 
-PROBE_KINDS = {"ffma": 0, "ffma2": 1, "imad": 2, "lop3": 3, "mufu_lg2": 4}
+PROBE_KINDS = {"ffma": 0, "ffma2": 1, "imad": 2, "lop3": 3, "mufu_lg2": 4, "philox": 5}
 
 
 def probe(kind: str, iters: int, blocks: int, sink: torch.Tensor, stream=None) -> int:

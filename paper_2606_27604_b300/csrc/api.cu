@@ -183,29 +183,50 @@ WalkConst make_const(const sss_params* p, const sss_walk_opts* o) {
 // Profiling events (per host thread).
 thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
 
-// Graph cache: one instantiated graph per exact argument set.
+// Graph cache: one instantiated graph per exact argument set, at most
+// kMaxGraphs of them (the oldest is dropped first).
+constexpr size_t kMaxGraphs = 64;
 std::map<std::string, cudaGraphExec_t> g_graphs;
+std::vector<std::string> g_graph_order;          // insertion order, oldest first
 std::map<cudaStream_t, const void*> g_last_ws;  // guarded by g_mu
 
+// Keys are built member by member (never from raw struct bytes, whose
+// padding is indeterminate), so equal arguments always give equal keys.
 template <class T>
 void put(std::string& k, const T& v) {
   k.append(reinterpret_cast<const char*>(&v), sizeof(T));
 }
 
+void put_params(std::string& k, const sss_params* p) {
+  put(k, p->alpha); put(k, p->sigma_t); put(k, p->g); put(k, p->w);
+  put(k, p->n_paths); put(k, p->uniform_paths); put(k, p->thickness_mm); put(k, p->n_rel);
+  put(k, p->K); put(k, p->n_inst);
+  put(k, p->alpha2); put(k, p->sigma_t2); put(k, p->g2); put(k, p->d1_mm);
+}
+
+void put_opts(std::string& k, const sss_walk_opts* o) {
+  put(k, o->nbins); put(k, o->r_max_mm); put(k, o->mode); put(k, o->rr_threshold);
+  put(k, o->entry_fresnel); put(k, o->max_steps); put(k, o->seed); put(k, o->path_offset);
+  put(k, o->want_sumsq); put(k, o->schedule); put(k, o->use_graph); put(k, o->block_threads);
+  put(k, o->unit_paths); put(k, o->regroup); put(k, o->instance_offset); put(k, o->incidence);
+  put(k, o->log_r_min_mm); put(k, o->select_pdf); put(k, o->hero_bands);
+  put(k, o->hero_texel_bands); put(k, o->hero_orbits);
+}
+
+// `ptrs` / `nptrs`: the output or gradient pointers of the call (structs of
+// pointers only, so their bytes have no padding).
 std::string graph_key(int tag, const sss_params* p, const sss_walk_opts* o, const void* ws,
-                      size_t wsb, const void* a, size_t an, const void* b, size_t bn,
-                      sss_stream_t st) {
+                      size_t wsb, const void* const* ptrs, size_t nptrs, sss_stream_t st) {
   std::string k;
   int dev = 0;
   cudaGetDevice(&dev);
   put(k, tag);
   put(k, dev);
-  put(k, *p);
-  put(k, *o);
+  put_params(k, p);
+  put_opts(k, o);
   put(k, ws);
   put(k, wsb);
-  k.append(reinterpret_cast<const char*>(a), an);
-  if (b) k.append(reinterpret_cast<const char*>(b), bn);
+  for (size_t i = 0; i < nptrs; ++i) put(k, ptrs[i]);
   put(k, st);
   return k;
 }
@@ -226,7 +247,8 @@ sss_status persistent_shape(bool adj, const sss_params* p, const sss_walk_opts* 
   // two slots of accumulators per warp; shrink the block for wide histograms
   // a hero group's slot holds its C members' accumulators
   const size_t members = o->hero_bands > 0 ? (size_t)o->hero_bands : 1;
-  const size_t per_warp = (size_t)2 * members * acc_words * 8 + 2 * kSlotMetaBytes;
+  const size_t per_warp =
+      (size_t)2 * members * acc_words * 8 + 2 * kSlotMetaBytes + kSelBufBytes;
   if (per_warp > kSmemLimit) return SSS_ERR_INVALID_ARG;
   const int max_warps = (int)(kSmemLimit / per_warp);
   if (sh->block / 32 > max_warps) sh->block = max_warps * 32;
@@ -309,6 +331,7 @@ sss_status enqueue_walk(bool adj, const sss_params* p, const sss_walk_opts* o, v
     t.steps = out->steps;
     t.truncated = reinterpret_cast<unsigned long long*>(out->truncated);
     t.raw_out = reinterpret_cast<unsigned long long*>(out->raw);
+    t.profile = out->profile;
   }
 
   if (p->n_inst > 0) {
@@ -383,12 +406,18 @@ sss_status run_impl(bool adj, const sss_params* p, const sss_walk_opts* o, void*
 
   std::string key;
   if (adj) {
-    key = graph_key(2, p, o, ws, wsb, gin ? (const void*)gin : (const void*)&key,
-                    gin ? sizeof(*gin) : 0, gout, sizeof(*gout), stream);
+    const void* ptrs[] = {gin ? gin->grad_R : nullptr, gin ? gin->grad_bins : nullptr,
+                          gin ? gin->grad_R_k : nullptr, gin ? gin->grad_T : nullptr,
+                          gout->d_alpha, gout->d_sigma_t, gout->d_g, gout->d_w,
+                          gout->d_alpha2, gout->d_sigma_t2, gout->d_g2};
+    key = graph_key(2, p, o, ws, wsb, ptrs, sizeof(ptrs) / sizeof(ptrs[0]), stream);
   } else {
     sss_tallies none{};
     const sss_tallies* tt = out ? out : &none;
-    key = graph_key(1, p, o, ws, wsb, tt, sizeof(*tt), nullptr, 0, stream);
+    const void* ptrs[] = {tt->R, tt->T, tt->A, tt->bins, tt->overflow, tt->R_k, tt->R1,
+                          tt->stderr_R, tt->stderr_bins, tt->truncated, tt->steps, tt->raw,
+                          tt->profile};
+    key = graph_key(1, p, o, ws, wsb, ptrs, sizeof(ptrs) / sizeof(ptrs[0]), stream);
   }
   cudaGraphExec_t exec = nullptr;
   {
@@ -419,7 +448,22 @@ sss_status run_impl(bool adj, const sss_params* p, const sss_walk_opts* o, void*
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return SSS_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
-    g_graphs[key] = exec;
+    auto it = g_graphs.find(key);
+    if (it != g_graphs.end()) {  // another thread built the same plan meanwhile
+      cudaGraphExecDestroy(exec);
+      exec = it->second;
+    } else {
+      if (g_graphs.size() >= kMaxGraphs) {  // drop the oldest plan
+        auto old = g_graphs.find(g_graph_order.front());
+        if (old != g_graphs.end()) {
+          cudaGraphExecDestroy(old->second);
+          g_graphs.erase(old);
+        }
+        g_graph_order.erase(g_graph_order.begin());
+      }
+      g_graphs[key] = exec;
+      g_graph_order.push_back(key);
+    }
   }
   return cudaGraphLaunch(exec, st) == cudaSuccess ? SSS_OK : SSS_ERR_CUDA;
 }
@@ -509,6 +553,7 @@ void sss_release_plans(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto& kv : g_graphs) cudaGraphExecDestroy(kv.second);
   g_graphs.clear();
+  g_graph_order.clear();
 }
 
 const char* sss_status_string(sss_status s) {

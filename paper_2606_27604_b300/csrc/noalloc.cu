@@ -13,8 +13,12 @@
 // The array is a file-scope __device__ variable, so every GPU that loads the
 // library holds SSS_NOALLOC_SCRATCH_BYTES of it until the process exits.  In
 // host code its name is only a host-side stand-in, not a device address; the
-// address is obtained once per device with cudaGetSymbolAddress (with that
-// device current) and cached.
+// address is obtained with cudaGetSymbolAddress (with the device current) on
+// the first call on a device and cached.  The cache is keyed by the CUDA
+// context's unique id as well, so after a cudaDeviceReset (which ends the
+// context and with it the array's old address) the next call looks the
+// address up again instead of handing a stale one to the kernels.
+#include <cuda.h>  // CUcontext / CUresult types only; driver calls go through entry points
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -29,19 +33,49 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SSS_NOALLOC_SCR
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx[kMaxDevices] = {0};
 
-// Device address of the scratch array on the current device (set up on the
-// first call for that device).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the current CUDA context, or 0 if there is none yet (or the
+// driver does not report one).
+unsigned long long current_context_id() {
+  static std::once_flag once;
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device: looked up on
+// the first call for that device (and again when its context has changed).
 sss_status scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SSS_ERR_UNSUPPORTED;
   if (dev < 0 || dev >= kMaxDevices) return SSS_ERR_UNSUPPORTED;
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
       return SSS_ERR_CUDA;
     g_addr[dev] = p;
+    g_ctx[dev] = ctx != 0 ? ctx : current_context_id();  // the lookup creates the context
   }
   *out = g_addr[dev];
   return SSS_OK;

@@ -213,9 +213,34 @@ __device__ __forceinline__ int select_medium(const WalkConst& c, uint32_t inst, 
   return c.K - 1;
 }
 
-// inst indexes the parameter arrays; the random-number counters use
-// instance number inst + instance_offset, or with OWN_CTR = false
-// `ctr_inst` (a hero group's first member).
+// Cosine-weighted incident lobe (incidence = 1): outside cosine sqrt(u),
+// azimuth 2 pi u', refracted by Snell's law; entry weight 1 - F at the
+// refracted angle, times the selection weight w_sel.  One Philox block with
+// tag 2 per path.
+__device__ __forceinline__ void entry_lobe(const WalkConst& c, uint32_t path, uint32_t cinst,
+                                           float w_sel, Path& p) {
+  const uint4 e = philox4x32_10_rk(make_uint4(0u, path, cinst, 2u), c.rk);
+  const float mu_o = sqrt_approx(u23(e.x));
+  const float sin_i = div_approx(sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu_o, mu_o, 1.0f))),
+                                 c.n_rel);
+  float sp, cp;
+  sincos_approx(__fmul_rn(6.2831853071795865f, __fsub_rn(u23(e.y), 0.5f)), &sp, &cp);
+  p.ux = -__fmul_rn(sin_i, cp);
+  p.uy = -__fmul_rn(sin_i, sp);
+  p.uz = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-sin_i, sin_i, 1.0f)));
+  p.W = __fmul_rn(c.entry_fresnel ? __fsub_rn(1.0f, fresnel(p.uz, c.n_rel)) : 1.0f, w_sel);
+}
+
+// Flight scale ln(2) / sigma_t of a medium (exponential flights use log2).
+__device__ __forceinline__ float flight_scale(float sigma_t) {
+  return __fmul_rn(0.693147180559945309f, __fdiv_rn(1.0f, sigma_t));
+}
+
+// Starts a path from global memory (the plain kernel and hero-wavelength
+// groups; the persistent kernel starts its paths from the media it staged
+// per unit, with the same arithmetic).  inst indexes the parameter arrays;
+// the random-number counters use instance number inst + instance_offset, or
+// with OWN_CTR = false `ctr_inst` (a hero group's first member).
 template <bool LAYERED = false, bool OWN_CTR = true>
 __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uint32_t path,
                                           float d, Path& p, uint32_t ctr_inst = 0) {
@@ -240,27 +265,14 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.k = k;
   p.alpha = __ldg(c.alpha + off);
   p.sigt = __ldg(c.sigma_t + off);
-  p.fl = __fmul_rn(0.693147180559945309f, __fdiv_rn(1.0f, p.sigt));
+  p.fl = flight_scale(p.sigt);
   p.g = __ldg(c.g + off);
   p.d = d;
   p.x = 0.0f; p.y = 0.0f; p.z = 0.0f;
   p.ux = 0.0f; p.uy = 0.0f; p.uz = 1.0f;
   p.W = __fmul_rn(c.W0, w_sel);
-  if (c.incidence == 1) {
-    // cosine-weighted incident lobe: outside cosine sqrt(u), azimuth 2 pi u',
-    // refracted by Snell's law; entry weight 1 - F at the refracted angle
-    const uint4 e = philox4x32_10_rk(
-        make_uint4(0u, path, OWN_CTR ? inst + c.inst_offset : ctr_inst, 2u), c.rk);
-    const float mu_o = sqrt_approx(u23(e.x));
-    const float sin_i = div_approx(sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu_o, mu_o, 1.0f))),
-                                   c.n_rel);
-    float sp, cp;
-    sincos_approx(__fmul_rn(6.2831853071795865f, __fsub_rn(u23(e.y), 0.5f)), &sp, &cp);
-    p.ux = -__fmul_rn(sin_i, cp);
-    p.uy = -__fmul_rn(sin_i, sp);
-    p.uz = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-sin_i, sin_i, 1.0f)));
-    p.W = __fmul_rn(c.entry_fresnel ? __fsub_rn(1.0f, fresnel(p.uz, c.n_rel)) : 1.0f, w_sel);
-  }
+  if (c.incidence == 1)
+    entry_lobe(c, path, OWN_CTR ? inst + c.inst_offset : ctr_inst, w_sel, p);
   p.Aacc = 0.0f;
   p.step = 0u;
   p.path = path;
@@ -277,7 +289,7 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
     p.d1 = __ldg(c.d1 + inst);
     p.a_o = __ldg(c.alpha2 + inst);
     p.sigt_o = __ldg(c.sigma_t2 + inst);
-    p.fl_o = __fmul_rn(0.693147180559945309f, __fdiv_rn(1.0f, p.sigt_o));
+    p.fl_o = flight_scale(p.sigt_o);
     p.g_o = __ldg(c.g2 + inst);
   }
 }

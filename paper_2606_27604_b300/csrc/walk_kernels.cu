@@ -201,14 +201,126 @@ __device__ __forceinline__ int grad_exponent(const WalkConst& c, const GradIn& g
 // Warp-uniform state of one work unit held by a warp (kept in shared memory).
 // `gen` counts the flushes of a slot: a lane whose path outlives its unit
 // (the slot was flushed, and perhaps refilled, meanwhile) sees another gen.
+// A unit is one instance, so its media are staged here once, when the unit
+// is taken: per medium (alpha, ln2 / sigma_t, g, sigma_t), the selection
+// thresholds and weights, and a second layer's optics.  Paths then start
+// from shared memory instead of re-reading and re-dividing per path.
 struct SlotMeta {
   uint32_t inst, next, end, live;
   float d, scale, lim, wsum;
   uint32_t gen, pad0, pad1, pad2;
+  float4 med[kKMax];     // alpha, ln2 / sigma_t, g, sigma_t per medium
+  float cdf[kKMax];      // running sum of w_k / sum(w): first K - 1 used
+  float wsel[kKMax];     // K w_k / sum(w) (uniform selection)
+  float4 l2;             // second layer: alpha, ln2 / sigma_t, g, sigma_t
+  float d1, pad3, pad4, pad5;
 };
 static_assert(sizeof(SlotMeta) == kSlotMetaBytes, "slot header size");
 
-enum : int { LANE_IDLE = 0, LANE_RUNNING = 1, LANE_DONE = 2 };
+// Per-warp buffer of medium choices: k[j] is the medium of path base + j of
+// the unit in slot `slot` (generation `gen`).  The 32 tag-1 Philox blocks
+// are drawn by the whole warp at once, so the draw runs with every lane
+// active instead of inside the refill's divergent block.
+struct SelBuf {
+  uint32_t base, slot, gen, valid;
+  uint8_t k[32];
+};
+static_assert(sizeof(SelBuf) == kSelBufBytes, "selection buffer size");
+
+// Loads the media of instance `inst` into slot header m: lane k < K reads
+// medium k (one load per array per lane), lane 0 forms the selection
+// thresholds in the order select_medium forms them, so a staged start is a
+// global-memory start bit for bit.
+template <bool LAYERED>
+__device__ __forceinline__ void stage_media(const WalkConst& c, uint32_t inst, int lane,
+                                            SlotMeta& m) {
+  float w = 0.0f;
+  if (lane < c.K) {
+    const size_t off = (size_t)lane * c.n_inst + inst;
+    const float a = __ldg(c.alpha + off), st = __ldg(c.sigma_t + off), g = __ldg(c.g + off);
+    w = __ldg(c.w + off);
+    m.med[lane] = make_float4(a, flight_scale(st), g, st);
+  }
+  float wk[kKMax];
+#pragma unroll
+  for (int k = 0; k < kKMax; ++k) wk[k] = __shfl_sync(kFull, w, k);
+  if (lane == 0) {
+    float total = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kKMax; ++k)
+      if (k < c.K) total = __fadd_rn(total, wk[k]);
+    const float inv = __fdiv_rn(1.0f, total);
+    float cdf = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kKMax; ++k) {
+      if (k < c.K) {
+        cdf = __fadd_rn(cdf, __fmul_rn(wk[k], inv));
+        m.cdf[k] = cdf;
+        m.wsel[k] = __fmul_rn(__fmul_rn((float)c.K, wk[k]), inv);
+      }
+    }
+    if (LAYERED) {
+      const float st2 = __ldg(c.sigma_t2 + inst);
+      m.l2 = make_float4(__ldg(c.alpha2 + inst), flight_scale(st2), __ldg(c.g2 + inst), st2);
+      m.d1 = __ldg(c.d1 + inst);
+    }
+  }
+}
+
+// Medium of a path from its tag-1 uniform u: the first k whose threshold
+// exceeds u (the last medium takes the remainder), or uniformly k = floor(u K).
+__device__ __forceinline__ int staged_choice(const WalkConst& c, const SlotMeta& m, float u) {
+  if (c.select_uniform) return min(c.K - 1, (int)__fmul_rn(u, (float)c.K));
+  int k = c.K - 1;
+#pragma unroll
+  for (int j = kKMax - 2; j >= 0; --j)
+    if (j < c.K - 1 && u < m.cdf[j]) k = j;
+  return k;
+}
+
+// Starts path `path` with medium k of the unit staged in m: the arithmetic
+// of path_init with the media read from shared memory.
+template <bool LAYERED>
+__device__ __forceinline__ void path_start(const WalkConst& c, const SlotMeta& m, int k,
+                                           uint32_t path, Path& p) {
+  const float4 md = m.med[k];
+  p.k = k;
+  p.alpha = md.x;
+  p.fl = md.y;
+  p.g = md.z;
+  p.sigt = md.w;
+  p.d = m.d;
+  p.x = 0.0f; p.y = 0.0f; p.z = 0.0f;
+  p.ux = 0.0f; p.uy = 0.0f; p.uz = 1.0f;
+  const float w_sel = c.select_uniform ? m.wsel[k] : 1.0f;
+  p.W = __fmul_rn(c.W0, w_sel);
+  const uint32_t inst = m.inst;
+  if (c.incidence == 1) entry_lobe(c, path, inst + c.inst_offset, w_sel, p);
+  p.Aacc = 0.0f;
+  p.step = 0u;
+  p.path = path;
+  p.inst = inst;
+  p.cinst = inst + c.inst_offset;
+  p.n_coll = 0u;
+  p.L = 0.0f;
+  p.G = 0.0f;
+  if (LAYERED) {
+    p.layer = 0;
+    p.n2 = 0u;
+    p.L2 = 0.0f;
+    p.G2 = 0.0f;
+    p.d1 = m.d1;
+    p.a_o = m.l2.x;
+    p.fl_o = m.l2.y;
+    p.g_o = m.l2.z;
+    p.sigt_o = m.l2.w;
+  }
+}
+
+// Lane state: idle, running, or done with exit event e (state 1 + e, e >= 1),
+// kept in one register.
+enum : int { LANE_IDLE = 0, LANE_RUNNING = 1 };
+__device__ __forceinline__ bool lane_done(int st) { return st > LANE_RUNNING; }
 
 // Adds one finished path to its slot's shared accumulators, or, when the
 // slot has moved on to another unit (`direct`), straight to the instance's
@@ -286,6 +398,96 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
   if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
 }
 
+// 64-bit shared-memory accumulation from native 32-bit atomics: the low
+// word's atomic returns its old value, so each adder sees whether its own
+// addition wrapped and carries it into the high word.  The 64-bit sum of a
+// word is exact once the adders are done (only the warp that owns the slot
+// touches it, and it reads the pair back after a __syncwarp).
+__device__ __forceinline__ void add64_shared(unsigned long long* a, unsigned long long v) {
+  uint32_t* w = reinterpret_cast<uint32_t*>(a);
+  const uint32_t lo = (uint32_t)v;
+  uint32_t hi = (uint32_t)(v >> 32);
+  if (lo != 0u) {
+    const uint32_t old = atomicAdd(w, lo);
+    hi += (uint32_t)(old + lo) < old ? 1u : 0u;
+  }
+  if (hi != 0u) atomicAdd(w + 1, hi);
+}
+
+// Exact sum of v < 2^59 over the lanes of `mask` (every lane of the mask
+// calls it): two 32-bit warp reductions of 27-bit pieces, which cannot wrap.
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned mask, unsigned long long v) {
+  const uint32_t lo = __reduce_add_sync(mask, (uint32_t)(v & 0x7FFFFFFull));
+  const uint32_t hi = __reduce_add_sync(mask, (uint32_t)(v >> 27));
+  return (unsigned long long)lo + ((unsigned long long)hi << 27);
+}
+
+// Forward exit tally of the finishing lanes of a warp (one-layer or
+// two-layer, no hero sharing).  Called by exactly the lanes of `done`.
+//  * Words every finishing lane adds to (absorbed weight A and the step
+//    count) are summed across the finishing lanes of each slot with warp
+//    reductions first; one lane then adds the sum to the slot's word.
+//  * Per-path words (radial bin, R_k, R1, T, squared weights) go to the
+//    slot with native 32-bit shared atomics (add64_shared).
+//  * A lane whose unit has been flushed meanwhile (`direct`) adds all its
+//    words straight to the instance's global accumulators.
+// Every word is an integer sum, so the result does not depend on how the
+// additions are grouped.
+__device__ __forceinline__ void tally_exit_warp(const WalkConst& c, const WalkSched& s,
+                                                const TallyOut& t, const Path& p, int ev,
+                                                unsigned long long* slot_mem, int myslot,
+                                                bool direct, unsigned done, int lane) {
+  const int nb = c.nbins, K = c.K, sw = s.slot_words;
+  const unsigned long long qa = p.Aacc > 0.0f ? to_fixed(p.Aacc) : 0ull;
+  const unsigned long long qs = (unsigned long long)p.step;
+  const int leader = __ffs(done) - 1;
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+    const bool in = !direct && myslot == o;
+    if (__ballot_sync(done, in) != 0u) {
+      const unsigned long long sa = warp_sum64(done, in ? qa : 0ull);
+      const unsigned long long ss = warp_sum64(done, in ? qs : 0ull);
+      if (lane == leader) {
+        unsigned long long* m = slot_mem + (size_t)o * sw;
+        m[nb + 3 + K] += sa;
+        m[nb + 5 + K] += ss;
+      }
+    }
+  }
+  if (!direct) {
+    unsigned long long* m = slot_mem + (size_t)myslot * sw;
+    if (ev == EV_TOP) {
+      const int bin = exit_bin(c, p);
+      const unsigned long long q = to_fixed(p.W);
+      add64_shared(m + bin, q);
+      add64_shared(m + nb + 1 + p.k, q);
+      if (p.n_coll == 1u) add64_shared(m + nb + 1 + K, q);
+      if (s.want_sumsq) add64_shared(m + nb + 6 + K + bin, to_fixed(__fmul_rn(p.W, p.W)));
+    } else if (ev == EV_BOTTOM) {
+      add64_shared(m + nb + 2 + K, to_fixed(p.W));
+    } else if (ev == EV_TRUNC) {
+      add64_shared(m + nb + 4 + K, 1ull);
+    }
+  } else {
+    unsigned long long* g = t.raw + (size_t)p.inst * sw;
+    if (ev == EV_TOP) {
+      const int bin = exit_bin(c, p);
+      const unsigned long long q = to_fixed(p.W);
+      atomicAdd(g + bin, q);
+      atomicAdd(g + nb + 1 + p.k, q);
+      if (p.n_coll == 1u) atomicAdd(g + nb + 1 + K, q);
+      if (s.want_sumsq) atomicAdd(g + nb + 6 + K + bin, to_fixed(__fmul_rn(p.W, p.W)));
+    } else if (ev == EV_BOTTOM) {
+      atomicAdd(g + nb + 2 + K, to_fixed(p.W));
+    } else if (ev == EV_TRUNC) {
+      atomicAdd(g + nb + 4 + K, 1ull);
+    }
+    if (qa) atomicAdd(g + nb + 3 + K, qa);
+    atomicAdd(g + nb + 5 + K, qs);
+  }
+  if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
+}
+
 // The forward one-layer kernel is held to 48 registers: five 256-thread
 // blocks per SM (40 warps) keep the issue slots busy.  HERO = C > 0: each
 // scheduled "instance" is a hero group of C bands, and a slot holds the C
@@ -293,7 +495,7 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
 template <bool ADJ, bool LAYERED, int HERO>
 __global__ void __launch_bounds__(256, HERO >= 4 ? 3 : ((ADJ || LAYERED || HERO) ? 4 : 5))
 walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
-  extern __shared__ unsigned long long smem[];
+  extern __shared__ __align__(16) unsigned long long smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -301,20 +503,21 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   unsigned long long* slot_mem = smem + (size_t)wib * 2 * slot_words;
   SlotMeta* meta =
       reinterpret_cast<SlotMeta*>(smem + (size_t)nwarps * 2 * slot_words) + 2 * wib;
+  SelBuf* sel = reinterpret_cast<SelBuf*>(reinterpret_cast<SlotMeta*>(
+                    smem + (size_t)nwarps * 2 * slot_words) + 2 * nwarps) + wib;
   for (int j = lane; j < 2 * slot_words; j += 32) slot_mem[j] = 0ull;
   if (lane < 2) {
     meta[lane].live = 0u;
     meta[lane].gen = 0u;
   }
+  if (lane == 0) sel->valid = 0u;
   __syncwarp();
 
   int cur = 0;        // slot new paths are drawn from (warp-uniform)
   bool more = true;   // the global queue may still hold units (warp-uniform)
 
   int st = LANE_IDLE;
-  int myslot = 0;
-  uint32_t mygen = 0;
-  int ev = EV_CONTINUE;
+  uint32_t mytag = 0;  // slot of the lane's path (bit 0) and that slot's generation
   Path p;
   p.step = 0;
   HeroState<HERO> hs;
@@ -337,8 +540,9 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
       for (int k = 0; k < c.K; ++k)
         wsum = __fadd_rn(wsum, __ldg(c.w + (size_t)k * c.n_inst + r.inst));
     }
+    if constexpr (HERO == 0) stage_media<LAYERED>(c, r.inst, lane, meta[o]);
     if (lane == 0) {
-      SlotMeta sm;
+      SlotMeta& sm = meta[o];
       sm.inst = r.inst;
       sm.next = r.p0;
       sm.end = r.p1;
@@ -349,9 +553,6 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
       sm.scale = scale;
       sm.lim = lim;
       sm.wsum = wsum;
-      sm.gen = meta[o].gen;
-      sm.pad0 = sm.pad1 = sm.pad2 = 0u;
-      meta[o] = sm;
     }
     __syncwarp();
     return true;
@@ -386,6 +587,20 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     __syncwarp();
   };
 
+  // Draws the medium choices of paths base .. base + 31 of slot o's unit.
+  auto fill_choices = [&](int o, uint32_t base) {
+    const uint4 r = philox4x32_10_rk(
+        make_uint4(0u, c.path_offset + base + lane, meta[o].inst + c.inst_offset, 1u), c.rk);
+    sel->k[lane] = (uint8_t)staged_choice(c, meta[o], u23(r.x));
+    if (lane == 0) {
+      sel->base = base;
+      sel->slot = (uint32_t)o;
+      sel->gen = meta[o].gen;
+      sel->valid = 1u;
+    }
+    __syncwarp();
+  };
+
   if (!fetch(0)) more = false;
 
   while (true) {
@@ -393,13 +608,23 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     const int n_nr = __popc(not_running);
     if (n_nr >= s.regroup || n_nr == 32) {
       // ---- 1. finished lanes tally together (one divergent block) ----
-      if (st == LANE_DONE) {
+      if constexpr (!ADJ && HERO == 0) {
+        const unsigned done = __ballot_sync(kFull, lane_done(st));
+        if (lane_done(st)) {
+          const int myslot = (int)(mytag & 1u);
+          tally_exit_warp(c, s, t, p, st - 1, slot_mem, myslot,
+                          meta[myslot].gen != (mytag >> 1), done, lane);
+          st = LANE_IDLE;
+        }
+      } else if (lane_done(st)) {
+        const int myslot = (int)(mytag & 1u);
+        const bool direct = meta[myslot].gen != (mytag >> 1);
         if constexpr (HERO > 0)
-          tally_path_hero<HERO>(c, s, t, p, hs, ev, slot_mem + (size_t)myslot * slot_words,
-                                meta[myslot].gen != mygen);
+          tally_path_hero<HERO>(c, s, t, p, hs, st - 1, slot_mem + (size_t)myslot * slot_words,
+                                direct);
         else
-          tally_path<ADJ, LAYERED>(c, s, gi, t, p, ev, slot_mem + (size_t)myslot * slot_words,
-                                   meta[myslot].gen != mygen);
+          tally_path<ADJ, LAYERED>(c, s, gi, t, p, st - 1,
+                                   slot_mem + (size_t)myslot * slot_words, direct);
         st = LANE_IDLE;
       }
       // ---- 2. refill idle lanes from the current unit (regrouping) ----
@@ -409,20 +634,25 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
         if (meta[cur].live && nxt < end) {
           const uint32_t take = min((uint32_t)__popc(idle), end - nxt);
           const int rank = __popc(idle & ((1u << lane) - 1u));
+          if constexpr (HERO == 0) {
+            if (!(sel->valid && sel->slot == (uint32_t)cur && sel->gen == meta[cur].gen &&
+                  sel->base <= nxt && nxt + take - sel->base <= 32u))
+              fill_choices(cur, nxt);
+          }
           __syncwarp();
           if (st == LANE_IDLE && (uint32_t)rank < take) {
             if constexpr (HERO > 0)
               hero_init<HERO>(c, meta[cur].inst, c.path_offset + nxt + rank, meta[cur].d, p, hs);
             else
-              path_init<LAYERED>(c, meta[cur].inst, c.path_offset + nxt + rank, meta[cur].d, p);
+              path_start<LAYERED>(c, meta[cur], sel->k[nxt + rank - sel->base],
+                                  c.path_offset + nxt + rank, p);
             if (ADJ) {
               p.gscale = meta[cur].scale;
               p.glim = meta[cur].lim;
               p.wsum = meta[cur].wsum;
             }
             st = LANE_RUNNING;
-            myslot = cur;
-            mygen = meta[cur].gen;
+            mytag = (meta[cur].gen << 1) | (uint32_t)cur;
           }
           __syncwarp();
           if (lane == 0) meta[cur].next = nxt + take;
@@ -449,8 +679,8 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     }
     // ---- advance every running path by one draw ----
     if (st == LANE_RUNNING) {
-      ev = path_step<ADJ, LAYERED, HERO>(c, p, hs);
-      if (ev != EV_CONTINUE) st = LANE_DONE;
+      const int ev = path_step<ADJ, LAYERED, HERO>(c, p, hs);
+      if (ev != EV_CONTINUE) st = LANE_RUNNING + ev;
     }
   }
   __syncwarp();
@@ -543,6 +773,10 @@ __global__ void finalize_tallies_kernel(WalkConst c, WalkSched s, TallyOut t) {
   }
   if (t.raw_out)
     for (int j = 0; j < nt; ++j) t.raw_out[(size_t)i * nt + j] = r[j];
+  if (t.profile) {  // P_d = bins / R (Eq. 3), from the exact integer sums
+    const double inv_R = sR ? 1.0 / (double)sR : 0.0;
+    for (int b = 0; b < nb; ++b) t.profile[(size_t)i * nb + b] = (double)r[b] * inv_R;
+  }
 }
 
 __global__ void finalize_grads_kernel(WalkConst c, GradIn gi, const unsigned long long* raw,

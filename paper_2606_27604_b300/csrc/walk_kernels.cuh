@@ -21,9 +21,28 @@ enum : unsigned int {
 constexpr float kFix = 4294967296.0f;  // 2^32
 constexpr double kInvFix = 1.0 / 4294967296.0;
 
-// Bytes of the per-slot header (SlotMeta) after a warp's two slots of
-// shared accumulators.
-constexpr int kSlotMetaBytes = 48;
+// round(W 2^32) for a weight 0 <= W < 2^31, the value __float2ull_rn gives,
+// built from the binary32 encoding so no 64-bit conversion instruction is
+// issued: x = W 2^32 is exact (power-of-two scale); below 2^23 adding 2^23
+// rounds x to an integer (to nearest, ties to even); from 2^23 up x is an
+// integer, its 24-bit significand shifted left by (exponent - 23).
+__device__ __forceinline__ unsigned long long to_fixed(float W) {
+  const float x = __fmul_rn(W, kFix);
+  const uint32_t small = __float_as_uint(__fadd_rn(x, 8388608.0f)) - 0x4B000000u;
+  const uint32_t b = __float_as_uint(x);
+  const unsigned long long big = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u)
+                                 << (((b >> 23) - 150u) & 63u);
+  return x < 8388608.0f ? (unsigned long long)small : big;
+}
+
+// Media per mixture the kernels support (SSS_KMAX of the public header).
+constexpr int kKMax = 4;
+
+// Bytes of the per-slot header (SlotMeta, with the unit's staged media)
+// after a warp's two slots of shared accumulators, and of the per-warp
+// buffer of medium choices (SelBuf) after the headers.
+constexpr int kSlotMetaBytes = 176;
+constexpr int kSelBufBytes = 48;
 
 struct WalkSched {
   unsigned long long* unit_counter;      // global work-queue head (zeroed per call)
@@ -42,6 +61,7 @@ struct TallyOut {
   double *R, *T, *A, *bins, *overflow, *R_k, *R1, *stderr_R, *stderr_bins, *steps;
   unsigned long long* truncated;
   unsigned long long* raw_out;
+  double* profile;   // bins / R (Eq. 3), or null
 };
 
 struct GradIn {

@@ -65,16 +65,16 @@ def build(alphas, gs, n_paths: int, nbins: int = 128, r_max: float = 32.0,
         t = lambda arr: torch.from_numpy(np.ascontiguousarray(arr[:, c0:c1])).to(dev)
         m = api.Media(t(a), t(s), t(g), t(w), None, n_paths, None, n_rel)
         o = api.WalkOptions(nbins=nbins, r_max_mm=r_max, seed=seed, instance_offset=c0)
-        out = api.walk(m, o)
+        d = lambda *shape: torch.empty(*shape, dtype=torch.float64, device=dev)
+        out = api.walk(m, o, out={"R": d(c1 - c0), "stderr_R": d(c1 - c0),
+                                  "profile": d(c1 - c0, nbins)})
         torch.cuda.synchronize(dev)
         code, flags = api.read_status(out["_workspace"])
         if code != 0:
             raise api.SSSError(code, "LUT walk")
-        Rc = out["R"].cpu().numpy()
-        R[c0:c1] = Rc
+        R[c0:c1] = out["R"].cpu().numpy()
         se[c0:c1] = out["stderr_R"].cpu().numpy()
-        with np.errstate(invalid="ignore", divide="ignore"):
-            P[c0:c1] = np.where(Rc[:, None] > 0, out["bins"].cpu().numpy() / Rc[:, None], 0.0)
+        P[c0:c1] = out["profile"].cpu().numpy()   # bins / R (Eq. 3), on the GPU
     na, ng = len(alphas), len(gs)
     return Lut(np.asarray(alphas, np.float64), np.asarray(gs, np.float64), r_max,
                R.reshape(na, ng), P.reshape(na, ng, nbins), se.reshape(na, ng), n_paths, n_rel)

@@ -50,7 +50,7 @@ def test_defaults_and_sizes(lib):
     assert o.entry_fresnel == 1 and o.want_sumsq == 1 and o.mode == 0
     assert lib.tally_count(64, 3, 1) == 64 + 6 + 3 + 65
     assert lib.tally_count(32, 3, 0) == 32 + 6 + 3
-    assert lib.abi_version() == 2
+    assert lib.abi_version() == 3
     # workspace size: header + accumulators, with a prefix table for uneven budgets
     p = lib.Params(C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), None,
                    4096, None, 1.4, 3, 1000)

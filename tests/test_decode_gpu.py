@@ -57,6 +57,43 @@ def test_decode_matches_reference(api, side):
     assert np.abs(g["alpha"] - r64["alpha"]).max() < 4 * np.sqrt(768) * 2 ** -8 * 0.25
 
 
+def test_decode_matches_reference_at_full_size_sampled(api):
+    # 600 x 600 = 360,000 texels: 2813 row tiles of 128 (the last one ragged),
+    # so every layer's persistent CTAs walk many tiles each and both TMEM
+    # accumulators and the accumulator-release wait run.  Decoding is row-
+    # independent, so the FP64 reference decodes only the sampled rows:
+    # every 173rd row, the whole ragged last tile and the rows around tile
+    # boundaries.
+    side = 600
+    T = side * side
+    import torch
+    W = inputs.decoder_weights(seed=4)
+    rgb = inputs.rgb_texture(side=side, seed=7)
+    out = api.decode(torch.from_numpy(rgb).cuda(), api.decoder_pack(W))
+    torch.cuda.synchronize()
+    code, flags = api.read_status(out["_workspace"])
+    assert code == 0 and flags == 0
+    last_tile = np.arange((T - 1) // 128 * 128, T)
+    edges = np.concatenate([np.arange(b - 2, b + 2) for b in range(128 * 500, T, 128 * 500)])
+    rows = np.unique(np.concatenate([np.arange(0, T, 173), last_tile, edges]))
+    assert len(rows) > 2000
+    r = dec_ref.decode(rgb[rows], W, bf16_activations=True)
+    n = len(rows)
+    cols = (np.arange(81)[:, None] * T + rows[None, :]).reshape(-1)   # band-major
+    ci = torch.from_numpy(cols).cuda()
+    g = {k: out[k][:, ci].cpu().numpy() for k in ("alpha", "g", "sigma_t", "w")}
+    for k in ("alpha", "g", "w"):
+        err = np.abs(g[k] - r[k])
+        print(k, "max abs err", err.max())
+        assert err.max() <= TOL_ABS, k
+    rel = np.abs(g["sigma_t"] / r["sigma_t"] - 1)
+    print("sigma_t max rel err", rel.max())
+    assert rel.max() <= TOL_SIG_REL
+    assert r["alpha"].shape == (3, 81 * n)
+    # the weights of every texel and band sum to one (all of them, on the GPU)
+    assert float((out["w"].sum(0) - 1.0).abs().max()) <= 1e-5
+
+
 def test_decode_feeds_the_walk(api):
     # the decoder's output is valid walk input (instances band-major)
     import torch

@@ -42,7 +42,13 @@ def test_extinction_rescales_the_radial_axis_exactly(lutmod):
     a, s, g, w = lutmod.grid_inputs(alphas, gs)
     t = lambda arr: torch.from_numpy(arr).cuda()
     m = api.Media(t(a), t(s * 4), t(g), t(w), None, 1 << 14, None, 1.4)
-    out = api.walk(m, api.WalkOptions(nbins=32, r_max_mm=4.0, seed=9))
+    o = api.WalkOptions(nbins=32, r_max_mm=4.0, seed=9)
+    out = api.alloc_tallies(m, o)
+    out["profile"] = torch.empty(m.n_inst, 32, dtype=torch.float64, device="cuda")
+    out = api.walk(m, o, out=out)
     R4 = out["R"].cpu().numpy()
     np.testing.assert_array_equal(R4, L.R.reshape(-1))
-    np.testing.assert_array_equal(out["bins"].cpu().numpy() / R4[:, None], L.P.reshape(-1, 32))
+    np.testing.assert_array_equal(out["profile"].cpu().numpy(), L.P.reshape(-1, 32))
+    # the profile output is bins / R (Eq. 3), up to the rounding of the quotient
+    np.testing.assert_allclose(out["profile"].cpu().numpy(),
+                               out["bins"].cpu().numpy() / R4[:, None], rtol=4e-16, atol=0)

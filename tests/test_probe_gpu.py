@@ -23,14 +23,15 @@ def test_probes_run_and_measure_plausible_rates(api):
     sink = torch.zeros(blocks * 256, dtype=torch.float32, device="cuda")
     rates = {}
     for kind in api.PROBE_KINDS:
-        iters = 1 << (12 if kind == "mufu_lg2" else 15)
+        iters = 1 << (12 if kind in ("mufu_lg2", "philox") else 15)
         api.probe(kind, 16, blocks, sink)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         ops = api.probe(kind, iters, blocks, sink)
         b.record()
         torch.cuda.synchronize()
-        assert ops == blocks * 256 * iters * (16 if kind == "ffma2" else 8)
+        per = {"ffma2": 16, "philox": 4}.get(kind, 8)
+        assert ops == blocks * 256 * iters * per
         rates[kind] = ops / (a.elapsed_time(b) / 1e3) / sms / 2.1e9  # lanes/clk/SM, clock <= 2.1 GHz
         if kind in ("ffma", "ffma2", "mufu_lg2"):
             assert torch.isfinite(sink).all(), kind
@@ -38,5 +39,8 @@ def test_probes_run_and_measure_plausible_rates(api):
     # an SM has 4 schedulers issuing at most one 32-lane instruction per clock
     assert rates["ffma"] <= 4 * 32 * 1.05 and rates["ffma"] > 32
     assert rates["mufu_lg2"] < rates["ffma"]
+    # a Philox4x32-10 block holds 20 32x32-bit products and 20 three-input
+    # XORs, so whole blocks issue far slower than single multiply-adds
+    assert 0 < rates["philox"] < rates["imad"] / 10
     with pytest.raises(api.SSSError):
         api.probe("ffma", 0, blocks, sink)

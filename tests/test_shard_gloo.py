@@ -1,8 +1,12 @@
 """Host-side multi-rank logic on CPU: world_size 2 over gloo.
 
-Each rank walks its contiguous range of instances with the FP64 oracle
-under the instances' global numbers (the GPU path takes the same numbers);
-the gathered result must equal a single-process walk of the whole batch,
+The ranks run the benchmark's own shard, walk and gather functions
+(paper_2606_27604_b300.shard), with the FP64 oracle as the walk, under the
+instances' global numbers (the GPU path takes the same numbers):
+  * strong sharding: one batch cut into contiguous instance ranges and one
+    all_gather must equal a single-process walk of the batch, bit for bit;
+  * weak sharding: each rank's own batch walked as its slice of a stacked
+    global batch must equal a single-process walk of the stacked batch;
 and the job time is the slowest rank's."""
 import os
 import socket
@@ -32,25 +36,47 @@ def _free_port():
     return p
 
 
-def _worker(rank, world, port, out_path):
+def _oracle_walk_fn(nbins=16, seed=3):
+    """A walk function for walk_and_gather: the FP64 oracle on CPU, under the
+    instances' global numbers, as the GPU walk takes them (instance_offset)."""
     import torch
-    import torch.distributed as dist
     import oracle
+
+    def fn(xs, begin):
+        r = oracle.walk(xs.alpha, xs.sigma_t, xs.g, xs.w, xs.n_paths, xs.thickness_mm, xs.n_rel,
+                        oracle.OracleOpts(nbins=nbins, seed=seed),
+                        inst_ids=np.arange(begin, begin + xs.n_inst))
+        return torch.from_numpy(r["R"]), torch.from_numpy(r["bins"])
+    return fn
+
+
+def _batch(seed=4):
     from paper_2606_27604_b300 import inputs
-    from paper_2606_27604_b300.shard import gather_instances, max_over_ranks, shard_range
+    return inputs.uneven_batch(n_inst=9, param_seed=seed, log2_min=8, log2_max=10)
+
+
+def _worker(rank, world, port, out_path):
+    # the shard, walk and gather steps of the benchmark's multi-GPU modes
+    import torch.distributed as dist
+    from paper_2606_27604_b300.shard import (gather_instances, max_over_ranks, shard_batch,
+                                             walk_and_gather)
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    x = inputs.uneven_batch(n_inst=9, param_seed=4, log2_min=8, log2_max=10)
-    b, e = shard_range(x.n_inst, rank, world)
-    xs = x.subset(np.arange(b, e))
-    r = oracle.walk(xs.alpha, xs.sigma_t, xs.g, xs.w, xs.n_paths, xs.thickness_mm, x.n_rel,
-                    oracle.OracleOpts(nbins=16, seed=3), inst_ids=np.arange(b, e))
-    local = torch.from_numpy(np.concatenate([r["R"][:, None], r["bins"]], axis=1))
-    full = gather_instances(local, x.n_inst)
+    fn = _oracle_walk_fn()
+    # strong: one batch cut into contiguous instance ranges, one all_gather
+    x = _batch()
+    xs, begin = shard_batch(x, rank, world)
+    full = walk_and_gather(fn, xs, begin, x.n_inst)
+    # weak: every rank walks its own batch as instances rank*n .. rank*n + n - 1
+    # of a global batch; no exchange during the walk (gathered here only to check)
+    xw = _batch(seed=10 + rank)
+    local = walk_and_gather(fn, xw, rank * xw.n_inst, xw.n_inst * world, gather=False)
+    weak = gather_instances(local, xw.n_inst * world)
     t = max_over_ranks(float(rank + 1))
     if rank == 0:
         np.save(out_path, full.numpy())
+        np.save(out_path + ".weak.npy", weak.numpy())
         np.save(out_path + ".t.npy", np.array([t]))
     dist.destroy_process_group()
 
@@ -62,9 +88,17 @@ def test_two_rank_walk_equals_single_process(tmp_path):
     out = str(tmp_path / "full.npy")
     mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True,
                        start_method="spawn")
-    got = np.load(out)
-    x = inputs.uneven_batch(n_inst=9, param_seed=4, log2_min=8, log2_max=10)
-    r = oracle.walk(x.alpha, x.sigma_t, x.g, x.w, x.n_paths, x.thickness_mm, x.n_rel,
-                    oracle.OracleOpts(nbins=16, seed=3))
-    np.testing.assert_array_equal(got, np.concatenate([r["R"][:, None], r["bins"]], axis=1))
+    fn = _oracle_walk_fn()
+    # strong sharding: the gathered table equals one process walking the batch
+    x = _batch()
+    R, bins = fn(x, 0)
+    np.testing.assert_array_equal(np.load(out), np.concatenate([R[:, None], bins], axis=1))
+    # weak sharding: equals one process walking the stacked batches
+    xa, xb = _batch(seed=10), _batch(seed=11)
+    stacked = inputs.WalkInputs(*(np.concatenate([getattr(xa, k), getattr(xb, k)], axis=-1)
+                                  for k in ("alpha", "sigma_t", "g", "w", "n_paths",
+                                            "thickness_mm")), n_rel=xa.n_rel)
+    R, bins = fn(stacked, 0)
+    np.testing.assert_array_equal(np.load(out + ".weak.npy"),
+                                  np.concatenate([R[:, None], bins], axis=1))
     assert np.load(out + ".t.npy")[0] == 2.0

@@ -357,6 +357,85 @@ def test_spectral_field_full_size_sampled(api):
     assert np.all(g["T"] == 0)   # semi-infinite
 
 
+def _full_field_sample(n_sample=16, seed=11):
+    """Instances sampled across the 256 x 256 x 81 field (first, last and
+    random ones) and their global instance numbers."""
+    x = inputs.spectral_field(n_texels=256 * 256, param_seed=1, n_paths=4096)
+    n = x.n_inst
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, n_sample - 2)]))
+    return x.subset(idx), idx
+
+
+def _walk_each_under_its_number(api, xs, idx, n_paths, **kw):
+    """GPU walk of each sampled instance at n_paths paths under its global
+    instance number (instance_offset), stacked like one batch."""
+    outs = []
+    for j, i in enumerate(idx):
+        xi = xs.subset([j])
+        xi.n_paths = np.full(1, n_paths, np.uint32)
+        g, code, flags = run_gpu(xi, opts(api, instance_offset=int(i), **kw), raw=True)
+        assert code == 0 and flags == 0
+        outs.append(g)
+    return {k: np.concatenate([o[k] for o in outs], axis=0) for k in outs[0]}
+
+
+def test_full_size_instances_at_2_18_paths_strict_bins(api):
+    # The full-size sampled test above runs at the benchmark's 4096 paths,
+    # where the same-stream floor (8 + 4e-6 N steps) / N is about 2e-3, as
+    # large as a tail bin.  Here 16 instances of the same field are re-walked
+    # at 2^18 paths under their own instance numbers on both sides: the floor
+    # drops to about 1.2e-4 and every one of the 64 bins is held to it.
+    xs, idx = _full_field_sample()
+    N = 1 << 18
+    g = _walk_each_under_its_number(api, xs, idx, N, nbins=64, r_max_mm=10.0, seed=1001)
+    xo = xs.subset(np.arange(len(idx)))
+    xo.n_paths = np.full(len(idx), N, np.uint32)
+    r = run_oracle(xo, opts(api, nbins=64, r_max_mm=10.0, seed=1001), inst_ids=idx)
+    worst, where = compare_same_stream(g, r, xo.n_paths, r["steps"])
+    print("same-stream worst ratio at 2^18 paths", worst, where)
+    assert worst <= 1.0, where
+    assert not compare_sigma(g, r, keys=("R", "bins", "R1", "A"))
+    # the tail bins carry weight, so the check bites there too
+    assert np.all(g["bins"][:, 48:].sum(1) > 0)
+
+
+def test_branch_flip_rate_per_draw(api):
+    # Measures the rate that the same-stream tolerance assumes (1e-6 per
+    # draw).  Analog mode: every exit carries the same weight W0, so the
+    # integer tallies count paths exactly.  A path whose binary32 trajectory
+    # ends in another outcome (radial bin, overflow, absorption) than the
+    # binary64 one moves one count between two outcomes; half the summed
+    # absolute count differences is the net number of such paths (a lower
+    # bound on the gross number, which can cancel within an outcome).
+    xs, idx = _full_field_sample(seed=12)
+    N = 1 << 18
+    kw = dict(nbins=64, r_max_mm=10.0, seed=1001, mode=1)
+    g = _walk_each_under_its_number(api, xs, idx, N, **kw)
+    xo = xs.subset(np.arange(len(idx)))
+    xo.n_paths = np.full(len(idx), N, np.uint32)
+    r = run_oracle(xo, opts(api, **kw), inst_ids=idx)
+    W0_32 = np.float32(1.0 - ((1.4 - 1) / 2.4) ** 2)
+    q0 = int(np.round(np.float64(W0_32) * 2.0 ** 32))
+    nb = 64
+    raw = g["raw"].astype(np.uint64)
+    K = 3
+    # GPU counts: bins + overflow (words 0..64) and absorbed (word nb + 3 + K)
+    cg = np.concatenate([raw[:, :nb + 1], raw[:, nb + 3 + K:nb + 4 + K]], axis=1)
+    assert np.all(cg % q0 == 0)
+    cg = (cg // q0).astype(np.int64)
+    W0 = 1.0 - ((1.4 - 1) / 2.4) ** 2
+    co = np.concatenate([r["bins"], r["overflow"][:, None], r["A"][:, None]], axis=1) * N / W0
+    assert np.allclose(co, np.round(co), atol=1e-6)
+    co = np.round(co).astype(np.int64)
+    assert np.all(cg.sum(1) == N) and np.all(co.sum(1) == N)
+    flips = np.abs(cg - co).sum() / 2.0
+    draws = float(np.sum(r["steps"] * N))
+    rate = flips / draws
+    print(f"net outcome flips {flips:.0f} over {draws:.3g} draws: {rate:.2e} per draw")
+    assert rate <= 1e-6
+
+
 def test_uneven_batch_sampled(api):
     x = inputs.uneven_batch(n_inst=4096, param_seed=2)
     o = opts(api, nbins=64, r_max_mm=10.0, seed=1002)

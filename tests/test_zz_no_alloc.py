@@ -48,6 +48,39 @@ def test_noalloc_matches_walk_on_two_calls_in_a_row(api):
     _compare(api, b, api.WalkOptions(nbins=32, r_max_mm=4.0, seed=6))
 
 
+def test_noalloc_without_a_flag_word_then_the_stream_status(api):
+    # status_flags = NULL: the call only enqueues; the device status of its
+    # scratch is then read through the per-stream status call
+    import torch
+    x = inputs.spectral_field(n_texels=3, param_seed=23, n_paths=2000)
+    o = api.WalkOptions(nbins=48, r_max_mm=8.0, seed=7)
+    m = api.Media.from_inputs(x)
+    ref = api.walk(m, o, raw=True)
+    out = api.alloc_tallies(m, o, raw=True)
+    code, flags = api.walk_noalloc(m, o, out, read_flags=False)
+    assert code == 0 and flags is None
+    code, flags = api.last_device_status()
+    assert code == 0 and flags == 0
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out["raw"].cpu().numpy(), ref["raw"].cpu().numpy())
+
+
+def test_noalloc_hero_and_no_sumsq_layouts(api):
+    # the other accumulator layouts: hero-wavelength groups (a slot holds
+    # three members' words) and tallies without squared weights
+    x = inputs.spectral_field(n_texels=2, param_seed=24, n_paths=1500)
+    _compare(api, x, api.WalkOptions(nbins=32, r_max_mm=6.0, seed=8, hero_bands=3,
+                                     hero_texel_bands=81))
+    o = api.WalkOptions(nbins=40, r_max_mm=7.0, seed=9, want_sumsq=0)
+    import torch
+    m = api.Media.from_inputs(x)
+    ref = api.walk(m, o, raw=True)
+    out = api.alloc_tallies(m, o, raw=True)
+    code, flags = api.walk_noalloc(m, o, out)
+    assert code == 0 and flags == 0
+    np.testing.assert_array_equal(out["raw"].cpu().numpy(), ref["raw"].cpu().numpy())
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch(api):
     x = inputs.spectral_field(n_texels=256, param_seed=1, n_paths=16)  # 20736 instances
     m = api.Media.from_inputs(x)
