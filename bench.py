@@ -37,9 +37,13 @@ UNIT = "paths/s"
 WORKLOAD = dict(workload="spectral_field_256x256x81", texels=256 * 256, bands=81,
                 paths_per_instance=4096, nbins=64, r_max_mm=10.0, n_rel=1.4,
                 slab="semi-infinite", K=3, param_seed=1, walk_seed=1001)
-# Algorithmic lane-operations of one walk step (one Philox block plus the
-# step's floating-point work); derivation in the design notes.
-ALG_ALU_OPS_PER_STEP = 120
+# Algorithmic lane-operations of one walk step: one Philox4x32-10 block
+# (10 rounds of two 32x32->64 multiplies, two XORs and the key bump, about
+# 60-70 integer lane-operations) plus the step's binary32 work (flight,
+# move, face test, weighting, Henyey-Greenstein, rotation, renormalisation,
+# about 40-50), about 110 in all; about 6 of the special-function unit.
+ALG_ALU_OPS_PER_STEP = 110
+ALG_FP32_OPS_PER_STEP = 50
 ALG_MUFU_OPS_PER_STEP = 6
 SM_LANES_PER_CLK = 128
 MUFU_LANES_PER_CLK = 16
@@ -379,8 +383,10 @@ def main():
     ap.add_argument("--fit", action="store_true", help="time the batched LUT fit instead")
     ap.add_argument("--fit-problems", type=int, default=1 << 16)
     ap.add_argument("--fit-steps", type=int, default=1000)
-    ap.add_argument("--autotune", action="store_true",
-                    help="pick the walk kernel's launch shape with the autotuner first")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the built-in launch shape instead of the autotuner's")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the walk directly instead of replaying a CUDA graph")
     ap.add_argument("--texels", type=int, default=WORKLOAD["texels"],
                     help="texels of the spectral field (smaller values: profiling cases)")
     ap.add_argument("--strong", action="store_true",
@@ -427,9 +433,15 @@ def main():
     m = api.Media.from_inputs(x, device=dev)
     o = api.WalkOptions(nbins=64, r_max_mm=10.0, seed=WORKLOAD["walk_seed"],
                         instance_offset=begin)
-    if args.autotune:
+    # launch shape from the autotuner (a sweep on a sample of this field),
+    # and the call replayed from a cached CUDA graph
+    if not args.no_autotune:
         from paper_2606_27604_b300 import autotune
         o = autotune.tune(m, o)
+    o_plain = o
+    if not args.no_graph:
+        from dataclasses import replace as _rep
+        o = _rep(o, use_graph=1)
     wsp = api.alloc_workspace(m, o)
     wsp_bytes = wsp.numel()
     out = api.alloc_tallies(m, o)
@@ -456,10 +468,6 @@ def main():
         raise RuntimeError(f"walk status {code} flags {flags}")
 
     # ---- device-timed region: inputs resident in HBM ----------------------
-    k_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    k_stop = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for e in k_start + k_stop:
-        e.record(stream)   # creates the CUDA events
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(dev.index)
     barrier()
@@ -467,12 +475,24 @@ def main():
     clocks.start()
     t0.record(stream)
     for i in range(args.steps):
-        api.profile_events(k_start[i], k_stop[i])
         step()
-    api.profile_events(None, None)
     t1.record(stream)
     torch.cuda.synchronize()
     barrier()
+    # the walk kernel alone (a graph replay cannot bracket one of its kernels):
+    # three launches of the same shape outside the graph, events around the
+    # kernel on its stream, while the clock sampler still runs
+    n_k = 3
+    k_start = [torch.cuda.Event(enable_timing=True) for _ in range(n_k)]
+    k_stop = [torch.cuda.Event(enable_timing=True) for _ in range(n_k)]
+    for e in k_start + k_stop:
+        e.record(stream)   # creates the CUDA events
+    torch.cuda.synchronize()
+    for i in range(n_k):
+        api.profile_events(k_start[i], k_stop[i])
+        api.walk(m, o_plain, workspace=wsp, out=out)
+    api.profile_events(None, None)
+    torch.cuda.synchronize()
     clk = clocks.stop()
     elapsed = t0.elapsed_time(t1) / 1e3
     kern = [a.elapsed_time(b) / 1e3 for a, b in zip(k_start, k_stop)]
@@ -582,11 +602,12 @@ def main():
         # for the whole field would be impractical): 2048 instances
         xs = x.subset(np.arange(2048))
         ms_ = api.Media.from_inputs(xs, device=dev)
-        wsb = api.alloc_workspace(ms_, o)
-        tsb = api.alloc_tallies(ms_, o)
+        wsb = api.alloc_workspace(ms_, o_plain)
+        tsb = api.alloc_tallies(ms_, o_plain)
         from dataclasses import replace as _rep
-        t_sub_plain = timed(lambda: api.walk(ms_, _rep(o, schedule=1), workspace=wsb, out=tsb))
-        t_sub_pers = timed(lambda: api.walk(ms_, o, workspace=wsb, out=tsb))
+        t_sub_plain = timed(lambda: api.walk(ms_, _rep(o_plain, schedule=1), workspace=wsb,
+                                             out=tsb))
+        t_sub_pers = timed(lambda: api.walk(ms_, o_plain, workspace=wsb, out=tsb))
         ps = 2048.0 * WORKLOAD["paths_per_instance"]
         baselines = {
             "uneven_batch": {"workload": "4096 instances, budgets floor(2^U[10,20]) "
@@ -606,7 +627,7 @@ def main():
     hero = None
     if not args.no_hero:
         from dataclasses import replace as _rep
-        oh = _rep(o, hero_bands=3, hero_texel_bands=81)
+        oh = _rep(o_plain, hero_bands=3, hero_texel_bands=81)
         wh = api.alloc_workspace(m, oh)
         th_ = api.alloc_tallies(m, oh)
         api.walk(m, oh, workspace=wh, out=th_)
@@ -687,7 +708,7 @@ def main():
         WORKLOAD["texels"] == 256 * 256 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "walk_persistent_kernel<false, false, 0>",
+                "kernel": "walk_persistent_kernel<false, false, 0, true> (semi-infinite slabs)",
                 "peak_basis": f"{sms} SMs x {SM_LANES_PER_CLK} FP32/INT32 lanes/clk x "
                               f"{f_mhz:.0f} MHz (median SM clock sampled in the timed region)",
                 "ops_per_step": ALG_ALU_OPS_PER_STEP, "steps_per_launch": total_draws,
@@ -702,7 +723,7 @@ def main():
                  "method": "8 independent chains per thread, 2048 threads per SM, "
                            "iteration loop unrolled 8x (loop control < 5% of issue)"}
         for kind, iters in (("ffma", 1 << 19), ("ffma2", 1 << 18), ("imad", 1 << 19),
-                            ("lop3", 1 << 19), ("mufu_lg2", 1 << 16)):
+                            ("lop3", 1 << 19), ("mufu_lg2", 1 << 16), ("philox", 1 << 14)):
             api.probe(kind, 64, blocks, sink, stream)   # warm-up
             pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             pa.record(stream)
@@ -714,6 +735,15 @@ def main():
         del sink
         roofline["peak_measured_ffma"] = sms * probe["ffma"] * f_mhz * 1e6 / 1e12
         roofline["frac_of_measured_ffma"] = achieved / roofline["peak_measured_ffma"]
+        # Philox-aware peak: a draw needs one Philox block (at the measured
+        # block rate, probe "philox" in blocks per clock per SM) plus its
+        # ~50 binary32 operations (at the measured FFMA rate), issued one
+        # after the other on the SM's schedulers
+        per_draw_clk = 1.0 / probe["philox"] + ALG_FP32_OPS_PER_STEP / probe["ffma"]
+        peak_draws = sms * f_mhz * 1e6 / per_draw_clk
+        roofline["peak_philox_aware_draws_per_s"] = peak_draws
+        roofline["draws_per_s"] = total_draws / kmean
+        roofline["frac_philox_aware"] = total_draws / kmean / peak_draws
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -735,7 +765,9 @@ def main():
             "adjoint_forward_ratio": ratio, "baselines": baselines, "hero_wavelength": hero,
             "probe": probe,
             "decoder": decoder, "pipeline": pipeline,
-            "launch_shape": {k: getattr(o, k) for k in ("block_threads", "unit_paths", "regroup")},
+            "launch_shape": dict({k: getattr(o, k) for k in ("block_threads", "unit_paths",
+                                                             "regroup")},
+                                 autotuned=not args.no_autotune, cuda_graph=bool(o.use_graph)),
             "status_flags": flags}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -253,7 +253,8 @@ sss_status persistent_shape(bool adj, const sss_params* p, const sss_walk_opts* 
   const int max_warps = (int)(kSmemLimit / per_warp);
   if (sh->block / 32 > max_warps) sh->block = max_warps * 32;
   sh->smem = (size_t)(sh->block / 32) * per_warp;
-  const void* fn = persistent_kernel_ptr(adj, p->alpha2 != nullptr, o->hero_bands);
+  const void* fn = persistent_kernel_ptr(adj, p->alpha2 != nullptr, o->hero_bands,
+                                         p->thickness_mm == nullptr);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit) !=
       cudaSuccess)
     return SSS_ERR_CUDA;

@@ -58,8 +58,24 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
 // 23 random bits k -> (k + 1/2) * 2^-23, exact in binary32, strictly in (0,1).
 // The bits become the mantissa of 1 + k 2^-23 in [1, 2); subtracting
 // 1 - 2^-24 (exact: both operands lie in [1/2, 2]) leaves (k + 1/2) 2^-23.
+// The top 23 bits are taken as the high word of x * 2^23 plus the encoding
+// of 1.0 in one integer multiply-add (the same bits as (x >> 9) | 0x3f800000,
+// since x >> 9 < 2^23), which issues on the multiply-add pipe instead of two
+// logic-unit operations.
 __device__ __forceinline__ float u23(uint32_t x) {
-  return __fsub_rn(__uint_as_float(0x3f800000u | (x >> 9)), 0.99999994039535522f);
+  uint32_t y;
+  asm("mad.hi.u32 %0, %1, 8388608, 1065353216;" : "=r"(y) : "r"(x));
+  return __fsub_rn(__uint_as_float(y), 0.99999994039535522f);
+}
+
+// Two uniforms at once: the same values as u23(a), u23(b), with the two
+// (exact) subtractions issued as one paired binary32 instruction.
+__device__ __forceinline__ float2 u23x2(uint32_t a, uint32_t b) {
+  uint32_t ya, yb;
+  asm("mad.hi.u32 %0, %1, 8388608, 1065353216;" : "=r"(ya) : "r"(a));
+  asm("mad.hi.u32 %0, %1, 8388608, 1065353216;" : "=r"(yb) : "r"(b));
+  return __fadd2_rn(make_float2(__uint_as_float(ya), __uint_as_float(yb)),
+                    make_float2(-0.99999994039535522f, -0.99999994039535522f));
 }
 
 // ------------------------------------------------------------ arguments --
@@ -175,12 +191,11 @@ __device__ __forceinline__ void sincos_approx(float x, float* sp, float* cp) {
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // Unpolarised Fresnel reflectance, medium (index n) -> outside (index 1),
-// without branches: total internal reflection (n sin_i >= 1) and n = 1 are
-// selected at the end; the two quotients share one reciprocal.
+// without branches: total internal reflection (sin^2 t = n^2 sin^2 i >= 1)
+// and n = 1 are selected at the end; the two quotients share one reciprocal.
 __device__ __forceinline__ float fresnel(float cos_i, float n) {
-  const float sin2_i = fmaxf(0.0f, __fmaf_rn(-cos_i, cos_i, 1.0f));
-  const float sin_t = __fmul_rn(n, sqrt_approx(sin2_i));
-  const float cos_t = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-sin_t, sin_t, 1.0f)));
+  const float sin2_t = __fmul_rn(__fmul_rn(n, n), __fmaf_rn(-cos_i, cos_i, 1.0f));
+  const float cos_t = sqrt_approx(fmaxf(0.0f, __fsub_rn(1.0f, sin2_t)));
   const float2 nc = __fmul2_rn(f2(n, n), f2(cos_i, cos_t));  // (n cos_i, n cos_t)
   const float2 sp = __fadd2_rn(f2(nc.x, cos_i), f2(cos_t, nc.y));  // (sd, pd)
   const float inv = rcp_approx(__fmul_rn(sp.x, sp.y));
@@ -188,7 +203,7 @@ __device__ __forceinline__ float fresnel(float cos_i, float n) {
   const float2 rr = __fmul2_rn(__fmul2_rn(df, f2(sp.y, sp.x)), f2(inv, inv));
   const float rs = rr.x, rp = rr.y;
   float F = __fmul_rn(0.5f, __fmaf_rn(rs, rs, __fmul_rn(rp, rp)));
-  F = sin_t >= 1.0f ? 1.0f : F;
+  F = sin2_t >= 1.0f ? 1.0f : F;
   return n == 1.0f ? 0.0f : F;
 }
 
@@ -297,17 +312,20 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
 // Henyey-Greenstein cosine by CDF inversion.  With xi = 2u - 1, the textbook
 // inverse  mu = (1 + g^2 - ((1-g^2)/(1+g xi))^2) / (2g)  is rewritten,
 // multiplying out and dividing by g, as the branch-free
-//   mu = ((1 + g^2)(2 xi + g xi^2) + g (3 - g^2)) / (2 (1 + g xi)^2),
+//   mu = ( (1 + g^2)/2 * xi (2 + g xi) + g (3 - g^2)/2 ) / (1 + g xi)^2,
 // exact for every g in (-1, 1) (g = 0 gives mu = xi) and free of the
 // 1/g cancellation of the textbook form at small g.  Lanes holding media
-// with different g run the same instructions.
+// with different g run the same instructions; independent pairs of
+// operations are issued as paired binary32 instructions.
 __device__ __forceinline__ float hg_mu(float g, float u) {
-  const float xi = __fsub_rn(__fmul_rn(2.0f, u), 1.0f);  // exact
+  const float xi = __fmaf_rn(2.0f, u, -1.0f);  // exact
+  const float2 t = __ffma2_rn(make_float2(g, g), make_float2(xi, xi),
+                              make_float2(2.0f, 1.0f));          // (2 + g xi, 1 + g xi)
   const float g2 = __fmul_rn(g, g);
-  const float a = __fmaf_rn(g, __fmul_rn(xi, xi), __fmul_rn(2.0f, xi));  // 2 xi + g xi^2
-  const float num = __fmaf_rn(__fadd_rn(1.0f, g2), a, __fmul_rn(g, __fsub_rn(3.0f, g2)));
-  const float den = __fmaf_rn(g, xi, 1.0f);
-  const float mu = div_approx(num, __fmul_rn(2.0f, __fmul_rn(den, den)));
+  const float2 h = __ffma2_rn(make_float2(g2, g2), make_float2(0.5f, -0.5f),
+                              make_float2(0.5f, 1.5f));          // ((1+g^2)/2, (3-g^2)/2)
+  const float num = __fmaf_rn(h.x, __fmul_rn(xi, t.x), __fmul_rn(g, h.y));
+  const float mu = div_approx(num, __fmul_rn(t.y, t.y));
   return fminf(1.0f, fmaxf(-1.0f, mu));
 }
 
@@ -322,13 +340,16 @@ __device__ __forceinline__ float hg_dlogp_dg(float g, float mu) {
 // Mostly branch-free: every lane evaluates both the face (Fresnel) and the
 // collision (weighting, Henyey-Greenstein, rotation) arithmetic and selects
 // the outcome of the event it actually met, so lanes of a warp that meet
-// different events issue the same instructions.
-template <bool ADJ, bool LAYERED = false, int HERO = 0>
+// different events issue the same instructions.  SEMI = true compiles the
+// semi-infinite slab (no far face: p.d is +inf), where only the entry face
+// can be met; the results are those of the general form for d = +inf.
+template <bool ADJ, bool LAYERED = false, int HERO = 0, bool SEMI = false>
 __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<HERO>& hs) {
   if (p.step >= c.max_steps) return EV_TRUNC;
   const uint4 r = philox4x32_10_rk(make_uint4(p.step, p.path, p.cinst, 0u), c.rk);
   p.step++;
-  const float u0 = u23(r.x), u1 = u23(r.y), u2 = u23(r.z), u3 = u23(r.w);
+  const float2 u01 = u23x2(r.x, r.y), u23_ = u23x2(r.z, r.w);
+  const float u0 = u01.x, u1 = u01.y, u2 = u23_.x, u3 = u23_.y;
 
   // Exponential free flight -ln(u0) / sigma_t, from the hardware log2
   // (absolute error <= 2^-22 mean free paths near u0 = 1, 2 ulp elsewhere).
@@ -339,7 +360,9 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
   float db;
   bool cross = false;  // reaches the internal interface of a two-layer slab
   const bool top = p.uz < 0.0f;
-  if (!LAYERED) {
+  if (SEMI) {
+    db = p.uz < 0.0f ? __fmul_rn(-p.z, iuz) : inf;
+  } else if (!LAYERED) {
     db = p.uz < 0.0f ? __fmul_rn(-p.z, iuz)
                      : (p.uz > 0.0f ? __fmul_rn(__fsub_rn(p.d, p.z), iuz) : inf);
   } else {
@@ -354,7 +377,8 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
   const float2 xy = __ffma2_rn(f2(dist, dist), f2(p.ux, p.uy), f2(p.x, p.y));
   p.x = xy.x;
   p.y = xy.y;
-  p.z = hit ? (cross ? p.d1 : (top ? 0.0f : p.d)) : __fmaf_rn(dist, p.uz, p.z);
+  if (SEMI) p.z = hit ? 0.0f : __fmaf_rn(dist, p.uz, p.z);  // a face hit is the top face
+  else p.z = hit ? (cross ? p.d1 : (top ? 0.0f : p.d)) : __fmaf_rn(dist, p.uz, p.z);
   if (ADJ) {
     if (LAYERED && p.layer) p.L2 = __fadd_rn(p.L2, dist);
     else p.L = __fadd_rn(p.L, dist);
@@ -367,8 +391,11 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
   // Collision: albedo weighting with roulette, or analog absorption.
   bool dead;
   if (c.mode == 0) {
-    const float Wn = __fmul_rn(p.W, p.alpha);
-    const float An = __fmaf_rn(p.W, __fsub_rn(1.0f, p.alpha), p.Aacc);
+    // (W alpha, W - W alpha) in one paired multiply-add
+    const float2 wa = __ffma2_rn(make_float2(p.W, p.W), make_float2(p.alpha, -p.alpha),
+                                 make_float2(0.0f, p.W));
+    const float Wn = wa.x;
+    const float An = __fadd_rn(wa.y, p.Aacc);
     if constexpr (HERO <= 1) {
       const bool low = Wn < c.rr_th;
       dead = !hit && low && !(u3 < __fmul_rn(Wn, c.inv_rr_th));
@@ -424,14 +451,15 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
   }
   // Azimuth phi = 2 pi u2; evaluated as phi - pi in (-pi, pi), then negated.
   float sp, cp;
-  sincos_approx(__fmul_rn(6.2831853071795865f, __fsub_rn(u2, 0.5f)), &sp, &cp);
+  sincos_approx(__fmaf_rn(u2, 6.2831853071795865f, -3.14159265358979324f), &sp, &cp);
   sp = -sp;
   cp = -cp;
-  const float st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
+  // mu is clamped to [-1, 1], so 1 - mu^2 (one rounding) is never negative
+  const float st = sqrt_approx(__fmaf_rn(-mu, mu, 1.0f));
   const float s2 = __fmaf_rn(-p.uz, p.uz, 1.0f);
   const float itmp = rsqrt_approx(s2);
-  const float tmp = __fmul_rn(s2, itmp);
-  const float sti = __fmul_rn(st, itmp);
+  const float2 ts = __fmul2_rn(make_float2(s2, st), make_float2(itmp, itmp));
+  const float tmp = ts.x, sti = ts.y;
   const float uzcp = __fmul_rn(p.uz, cp);
   const bool polar = fabsf(p.uz) > 0.999999f;
   // (nx, ny) off the pole: sti (u_xy uz cp -+ u_yx sp) + u_xy mu, in pairs
@@ -460,7 +488,7 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
     return EV_CONTINUE;
   }
   if (dead) return EV_DEAD;
-  if (hit && !reflect) return top ? EV_TOP : EV_BOTTOM;
+  if (hit && !reflect) return (SEMI || top) ? EV_TOP : EV_BOTTOM;
   return EV_CONTINUE;
 }
 

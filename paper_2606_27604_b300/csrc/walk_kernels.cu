@@ -492,8 +492,10 @@ __device__ __forceinline__ void tally_exit_warp(const WalkConst& c, const WalkSc
 // blocks per SM (40 warps) keep the issue slots busy.  HERO = C > 0: each
 // scheduled "instance" is a hero group of C bands, and a slot holds the C
 // members' accumulators.
-template <bool ADJ, bool LAYERED, int HERO>
-__global__ void __launch_bounds__(256, HERO >= 4 ? 3 : ((ADJ || LAYERED || HERO) ? 4 : 5))
+// SEMI: every instance is a semi-infinite slab (no thickness array).
+template <bool ADJ, bool LAYERED, int HERO, bool SEMI>
+__global__ void __launch_bounds__(256, (HERO >= 4 || (ADJ && LAYERED))
+                                           ? 3 : ((ADJ || LAYERED || HERO) ? 4 : 5))
 walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   extern __shared__ __align__(16) unsigned long long smem[];
   const int lane = threadIdx.x & 31;
@@ -679,7 +681,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     }
     // ---- advance every running path by one draw ----
     if (st == LANE_RUNNING) {
-      const int ev = path_step<ADJ, LAYERED, HERO>(c, p, hs);
+      const int ev = path_step<ADJ, LAYERED, HERO, SEMI>(c, p, hs);
       if (ev != EV_CONTINUE) st = LANE_RUNNING + ev;
     }
   }
@@ -849,24 +851,30 @@ void launch_unit_prefix(const uint32_t* n_paths, uint32_t n, uint32_t C,
 void launch_walk_persistent(bool adj, int grid, int block, size_t smem, const WalkConst& c,
                             const WalkSched& s, const TallyOut& t, const GradIn& gi,
                             cudaStream_t st) {
-  const void* fn = persistent_kernel_ptr(adj, c.alpha2 != nullptr, c.hero);
+  const void* fn = persistent_kernel_ptr(adj, c.alpha2 != nullptr, c.hero,
+                                         c.thickness == nullptr);
   void* args[] = {const_cast<WalkConst*>(&c), const_cast<WalkSched*>(&s),
                   const_cast<TallyOut*>(&t), const_cast<GradIn*>(&gi)};
   cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
-const void* persistent_kernel_ptr(bool adj, bool layered, int hero) {
+// Semi-infinite batches (no thickness array) take the SEMI instantiations;
+// two-layer slabs keep the general one.
+const void* persistent_kernel_ptr(bool adj, bool layered, int hero, bool semi) {
+#define SSS_K(A, L, H) (semi ? (const void*)walk_persistent_kernel<A, L, H, true> \
+                             : (const void*)walk_persistent_kernel<A, L, H, false>)
   if (adj)
-    return layered ? (const void*)walk_persistent_kernel<true, true, 0>
-                   : (const void*)walk_persistent_kernel<true, false, 0>;
-  if (layered) return (const void*)walk_persistent_kernel<false, true, 0>;
+    return layered ? (const void*)walk_persistent_kernel<true, true, 0, false>
+                   : SSS_K(true, false, 0);
+  if (layered) return (const void*)walk_persistent_kernel<false, true, 0, false>;
   switch (hero) {
-    case 1: return (const void*)walk_persistent_kernel<false, false, 1>;
-    case 2: return (const void*)walk_persistent_kernel<false, false, 2>;
-    case 3: return (const void*)walk_persistent_kernel<false, false, 3>;
-    case 4: return (const void*)walk_persistent_kernel<false, false, 4>;
-    default: return (const void*)walk_persistent_kernel<false, false, 0>;
+    case 1: return SSS_K(false, false, 1);
+    case 2: return SSS_K(false, false, 2);
+    case 3: return SSS_K(false, false, 3);
+    case 4: return SSS_K(false, false, 4);
+    default: return SSS_K(false, false, 0);
   }
+#undef SSS_K
 }
 
 void launch_walk_plain(const WalkConst& c, const WalkSched& s, const TallyOut& t, uint32_t inst,
