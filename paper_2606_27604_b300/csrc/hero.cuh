@@ -117,7 +117,7 @@ __device__ __forceinline__ void tally_path_hero(const WalkConst& c, const WalkSc
   const int nb = c.nbins, sw = s.slot_words;
   const HeroGroup G = direct ? hero_group<C>(c, p.inst) : HeroGroup{0u, 0u};
   auto add = [&](int j, int w, unsigned long long v) {
-    if (!direct) atomicAdd(m + j * sw + w, v);
+    if (!direct) add64_shared(m + j * sw + w, v);
     else atomicAdd(t.raw + (size_t)(G.first + (uint32_t)j * G.stride) * sw + w, v);
   };
   float F[C];

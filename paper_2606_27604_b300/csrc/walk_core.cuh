@@ -55,6 +55,49 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
   return c;
 }
 
+// A walk step's block, with its first two rounds partly done per path.  The
+// step counter is (step, path, instance, 0).  In round 1 the product
+// instance * M1 does not depend on the step, and neither does round 1's
+// lane-x output x1 = hi(instance * M1) ^ path ^ k0; in round 2 the product
+// x1 * M0 is then also a per-path constant.  So at the start of a path
+//   b1 = lo(instance * M1),  e2 = hi(x1 * M0) ^ (round-2 key 1),  f2 = lo(x1 * M0)
+// are formed once (philox_path), and a step (philox_step) computes rounds
+// 1-2 from them and rounds 3-10 as usual: the same Philox4x32-10 block as
+// philox4x32_10_rk, with two 32x32->64 products and one XOR fewer per draw.
+struct PhiloxPath {
+  uint32_t b1, e2, f2;
+};
+
+__device__ __forceinline__ PhiloxPath philox_path(uint32_t path, uint32_t cinst,
+                                                  const uint32_t* rk) {
+  const unsigned long long p1 = (unsigned long long)cinst * 0xCD9E8D57ull;
+  const uint32_t x1 = (uint32_t)(p1 >> 32) ^ path ^ rk[0];
+  const unsigned long long q0 = (unsigned long long)x1 * 0xD2511F53ull;
+  PhiloxPath r;
+  r.b1 = (uint32_t)p1;
+  r.e2 = (uint32_t)(q0 >> 32) ^ rk[3];
+  r.f2 = (uint32_t)q0;
+  return r;
+}
+
+__device__ __forceinline__ uint4 philox_step(uint32_t step, const PhiloxPath& pc,
+                                             const uint32_t* rk) {
+  // round 1: (step, path, instance, 0) -> (x1, b1, z1, w1)
+  const unsigned long long p0 = (unsigned long long)step * 0xD2511F53ull;
+  const uint32_t z1 = (uint32_t)(p0 >> 32) ^ rk[1], w1 = (uint32_t)p0;
+  // round 2: products x1 * M0 (per path) and z1 * M1
+  const unsigned long long p1 = (unsigned long long)z1 * 0xCD9E8D57ull;
+  uint4 c = make_uint4((uint32_t)(p1 >> 32) ^ pc.b1 ^ rk[2], (uint32_t)p1, pc.e2 ^ w1, pc.f2);
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    const unsigned long long q0 = (unsigned long long)c.x * 0xD2511F53ull;
+    const unsigned long long q1 = (unsigned long long)c.z * 0xCD9E8D57ull;
+    c = make_uint4((uint32_t)(q1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)q1,
+                   (uint32_t)(q0 >> 32) ^ c.w ^ rk[2 * r + 1], (uint32_t)q0);
+  }
+  return c;
+}
+
 // 23 random bits k -> (k + 1/2) * 2^-23, exact in binary32, strictly in (0,1).
 // The bits become the mantissa of 1 + k 2^-23 in [1, 2); subtracting
 // 1 - 2^-24 (exact: both operands lie in [1/2, 2]) leaves (k + 1/2) 2^-23.
@@ -124,8 +167,8 @@ struct Path {
   float W;        // current weight
   float Aacc;     // weight deposited by collisions
   float alpha, sigt, fl, g, d;  // fl = ln(2) / sigma_t (flight scale for log2)
-  uint32_t step, path, inst, n_coll;
-  uint32_t cinst;  // instance number in the random-number counters
+  uint32_t step, inst, n_coll;
+  PhiloxPath pc;  // per-path constants of the step blocks' counters (philox_path)
   int k;
   float L;        // path length inside the medium (adjoint; top layer if layered)
   float G;        // sum of d log p_HG / d g (adjoint; top layer if layered)
@@ -135,7 +178,15 @@ struct Path {
   float a_o, fl_o, g_o, sigt_o, d1;
   int layer;
   float gscale, glim, wsum;  // adjoint: fixed-point scale, per-path limit, sum(w)
+  float hc1, hc2;  // Henyey-Greenstein constants of g (hg_consts)
 };
+
+// The per-medium constants of the Henyey-Greenstein inversion (hg_mu):
+// ((1 + g^2) / 2, g (3 - g^2) / 2), formed once per medium or path.
+__device__ __forceinline__ float2 hg_consts(float g) {
+  const float g2 = __fmul_rn(g, g);
+  return make_float2(__fmaf_rn(g2, 0.5f, 0.5f), __fmul_rn(g, __fmaf_rn(g2, -0.5f, 1.5f)));
+}
 
 // Hero-wavelength sharing state of a path of a group of C members: the hero
 // index h and, for the other members m (member (h + 1 + m) mod C), weight W,
@@ -282,6 +333,9 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   p.sigt = __ldg(c.sigma_t + off);
   p.fl = flight_scale(p.sigt);
   p.g = __ldg(c.g + off);
+  const float2 hc = hg_consts(p.g);
+  p.hc1 = hc.x;
+  p.hc2 = hc.y;
   p.d = d;
   p.x = 0.0f; p.y = 0.0f; p.z = 0.0f;
   p.ux = 0.0f; p.uy = 0.0f; p.uz = 1.0f;
@@ -290,9 +344,8 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
     entry_lobe(c, path, OWN_CTR ? inst + c.inst_offset : ctr_inst, w_sel, p);
   p.Aacc = 0.0f;
   p.step = 0u;
-  p.path = path;
   p.inst = inst;
-  p.cinst = OWN_CTR ? inst + c.inst_offset : ctr_inst;
+  p.pc = philox_path(path, OWN_CTR ? inst + c.inst_offset : ctr_inst, c.rk);
   p.n_coll = 0u;
   p.L = 0.0f;
   p.G = 0.0f;
@@ -315,17 +368,12 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
 //   mu = ( (1 + g^2)/2 * xi (2 + g xi) + g (3 - g^2)/2 ) / (1 + g xi)^2,
 // exact for every g in (-1, 1) (g = 0 gives mu = xi) and free of the
 // 1/g cancellation of the textbook form at small g.  Lanes holding media
-// with different g run the same instructions; independent pairs of
-// operations are issued as paired binary32 instructions.
-__device__ __forceinline__ float hg_mu(float g, float u) {
+// with different g run the same instructions.  hc1, hc2 = hg_consts(g).
+__device__ __forceinline__ float hg_mu(float g, float hc1, float hc2, float u) {
   const float xi = __fmaf_rn(2.0f, u, -1.0f);  // exact
-  const float2 t = __ffma2_rn(make_float2(g, g), make_float2(xi, xi),
-                              make_float2(2.0f, 1.0f));          // (2 + g xi, 1 + g xi)
-  const float g2 = __fmul_rn(g, g);
-  const float2 h = __ffma2_rn(make_float2(g2, g2), make_float2(0.5f, -0.5f),
-                              make_float2(0.5f, 1.5f));          // ((1+g^2)/2, (3-g^2)/2)
-  const float num = __fmaf_rn(h.x, __fmul_rn(xi, t.x), __fmul_rn(g, h.y));
-  const float mu = div_approx(num, __fmul_rn(t.y, t.y));
+  const float tx = __fmaf_rn(g, xi, 2.0f), ty = __fmaf_rn(g, xi, 1.0f);  // 2 + g xi, 1 + g xi
+  const float num = __fmaf_rn(hc1, __fmul_rn(xi, tx), hc2);
+  const float mu = div_approx(num, __fmul_rn(ty, ty));
   return fminf(1.0f, fmaxf(-1.0f, mu));
 }
 
@@ -346,7 +394,7 @@ __device__ __forceinline__ float hg_dlogp_dg(float g, float mu) {
 template <bool ADJ, bool LAYERED = false, int HERO = 0, bool SEMI = false>
 __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<HERO>& hs) {
   if (p.step >= c.max_steps) return EV_TRUNC;
-  const uint4 r = philox4x32_10_rk(make_uint4(p.step, p.path, p.cinst, 0u), c.rk);
+  const uint4 r = philox_step(p.step, p.pc, c.rk);
   p.step++;
   const float2 u01 = u23x2(r.x, r.y), u23_ = u23x2(r.z, r.w);
   const float u0 = u01.x, u1 = u01.y, u2 = u23_.x, u3 = u23_.y;
@@ -391,11 +439,9 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
   // Collision: albedo weighting with roulette, or analog absorption.
   bool dead;
   if (c.mode == 0) {
-    // (W alpha, W - W alpha) in one paired multiply-add
-    const float2 wa = __ffma2_rn(make_float2(p.W, p.W), make_float2(p.alpha, -p.alpha),
-                                 make_float2(0.0f, p.W));
-    const float Wn = wa.x;
-    const float An = __fadd_rn(wa.y, p.Aacc);
+    // the surviving weight W alpha and the deposit W - W alpha (one rounding)
+    const float Wn = __fmul_rn(p.W, p.alpha);
+    const float An = __fadd_rn(__fmaf_rn(p.W, -p.alpha, p.W), p.Aacc);
     if constexpr (HERO <= 1) {
       const bool low = Wn < c.rr_th;
       dead = !hit && low && !(u3 < __fmul_rn(Wn, c.inv_rr_th));
@@ -431,7 +477,7 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
   if (ADJ && LAYERED) p.n2 += (hit || !p.layer) ? 0u : 1u;
 
   // Henyey-Greenstein scattering with this medium's g.
-  const float mu = hg_mu(p.g, u1);
+  const float mu = hg_mu(p.g, p.hc1, p.hc2, u1);
   if constexpr (HERO > 1) {
     // log2 p_HG(mu; g_m) - log2 p_HG(mu; g_h)
     //   = log2((1-g_m^2)/(1-g_h^2)) - 1.5 (log2(1+g_m^2-2 g_m mu) - log2(1+g_h^2-2 g_h mu))
@@ -483,6 +529,9 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
     t = p.alpha; p.alpha = p.a_o; p.a_o = t;
     t = p.fl; p.fl = p.fl_o; p.fl_o = t;
     t = p.g; p.g = p.g_o; p.g_o = t;
+    const float2 hc = hg_consts(p.g);  // the new layer's Henyey-Greenstein constants
+    p.hc1 = hc.x;
+    p.hc2 = hc.y;
     t = p.sigt; p.sigt = p.sigt_o; p.sigt_o = t;
     p.layer ^= 1;
     return EV_CONTINUE;

@@ -199,31 +199,38 @@ __device__ __forceinline__ int grad_exponent(const WalkConst& c, const GradIn& g
 }
 
 // Warp-uniform state of one work unit held by a warp (kept in shared memory).
-// `gen` counts the flushes of a slot: a lane whose path outlives its unit
-// (the slot was flushed, and perhaps refilled, meanwhile) sees another gen.
+// `gl` holds the slot's generation (the number of its flushes) times two
+// plus a live bit: a lane whose path outlives its unit (the slot was
+// flushed, and perhaps refilled, meanwhile) sees another generation.  The
+// first 16 bytes (inst, next, end, gl) are what the refill loop reads, in
+// one vector load.
 // A unit is one instance, so its media are staged here once, when the unit
 // is taken: per medium (alpha, ln2 / sigma_t, g, sigma_t), the selection
 // thresholds and weights, and a second layer's optics.  Paths then start
 // from shared memory instead of re-reading and re-dividing per path.
 struct SlotMeta {
-  uint32_t inst, next, end, live;
+  uint32_t inst, next, end, gl;
   float d, scale, lim, wsum;
-  uint32_t gen, pad0, pad1, pad2;
+  uint32_t spare0, spare1, spare2, spare3;
   float4 med[kKMax];     // alpha, ln2 / sigma_t, g, sigma_t per medium
   float cdf[kKMax];      // running sum of w_k / sum(w): first K - 1 used
   float wsel[kKMax];     // K w_k / sum(w) (uniform selection)
   float4 l2;             // second layer: alpha, ln2 / sigma_t, g, sigma_t
   float d1, pad3, pad4, pad5;
+  float2 hgc[kKMax];     // hg_consts(g) per medium
 };
 static_assert(sizeof(SlotMeta) == kSlotMetaBytes, "slot header size");
 
 // Per-warp buffer of medium choices: k[j] is the medium of path base + j of
-// the unit in slot `slot` (generation `gen`).  The 32 tag-1 Philox blocks
-// are drawn by the whole warp at once, so the draw runs with every lane
-// active instead of inside the refill's divergent block.
+// the warp's current unit (the buffer is invalidated whenever the warp takes
+// a unit).  The 32 tag-1 Philox blocks are drawn by the whole warp at once,
+// so the draw runs with every lane active instead of inside the refill's
+// divergent block.
 struct SelBuf {
-  uint32_t base, slot, gen, valid;
+  uint32_t base, valid, pad0, pad1;
   uint8_t k[32];
+  uint32_t inst[32];  // instance of each lane's path (read only by a direct tally; the
+                      // forward kernel keeps it here instead of in a register)
 };
 static_assert(sizeof(SelBuf) == kSelBufBytes, "selection buffer size");
 
@@ -240,6 +247,7 @@ __device__ __forceinline__ void stage_media(const WalkConst& c, uint32_t inst, i
     const float a = __ldg(c.alpha + off), st = __ldg(c.sigma_t + off), g = __ldg(c.g + off);
     w = __ldg(c.w + off);
     m.med[lane] = make_float4(a, flight_scale(st), g, st);
+    m.hgc[lane] = hg_consts(g);
   }
   float wk[kKMax];
 #pragma unroll
@@ -278,29 +286,30 @@ __device__ __forceinline__ int staged_choice(const WalkConst& c, const SlotMeta&
   return k;
 }
 
-// Starts path `path` with medium k of the unit staged in m: the arithmetic
-// of path_init with the media read from shared memory.
+// Starts path `path` with medium k of the unit (instance inst) staged in m:
+// the arithmetic of path_init with the media read from shared memory.
 template <bool LAYERED>
-__device__ __forceinline__ void path_start(const WalkConst& c, const SlotMeta& m, int k,
-                                           uint32_t path, Path& p) {
+__device__ __forceinline__ void path_start(const WalkConst& c, const SlotMeta& m, uint32_t inst,
+                                           int k, uint32_t path, Path& p) {
   const float4 md = m.med[k];
   p.k = k;
   p.alpha = md.x;
   p.fl = md.y;
   p.g = md.z;
   p.sigt = md.w;
+  const float2 hc = m.hgc[k];
+  p.hc1 = hc.x;
+  p.hc2 = hc.y;
   p.d = m.d;
   p.x = 0.0f; p.y = 0.0f; p.z = 0.0f;
   p.ux = 0.0f; p.uy = 0.0f; p.uz = 1.0f;
   const float w_sel = c.select_uniform ? m.wsel[k] : 1.0f;
   p.W = __fmul_rn(c.W0, w_sel);
-  const uint32_t inst = m.inst;
   if (c.incidence == 1) entry_lobe(c, path, inst + c.inst_offset, w_sel, p);
   p.Aacc = 0.0f;
   p.step = 0u;
-  p.path = path;
   p.inst = inst;
-  p.cinst = inst + c.inst_offset;
+  p.pc = philox_path(path, inst + c.inst_offset, c.rk);
   p.n_coll = 0u;
   p.L = 0.0f;
   p.G = 0.0f;
@@ -330,7 +339,7 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
                                            const GradIn& gi, const TallyOut& t, const Path& p,
                                            int ev, unsigned long long* m, bool direct) {
   auto add = [&](int j, unsigned long long v) {
-    if (!direct) atomicAdd(m + j, v);
+    if (!direct) add64_shared(m + j, v);  // (two's complement: signed words too)
     else if (ADJ) atomicAdd(t.raw + (size_t)j * c.n_inst + p.inst, v);
     else atomicAdd(t.raw + (size_t)p.inst * s.slot_words + j, v);
   };
@@ -398,22 +407,6 @@ __device__ __forceinline__ void tally_path(const WalkConst& c, const WalkSched& 
   if (ev == EV_TRUNC) atomicOr(s.status, SSS_DEV_FLAG_STEP_LIMIT);
 }
 
-// 64-bit shared-memory accumulation from native 32-bit atomics: the low
-// word's atomic returns its old value, so each adder sees whether its own
-// addition wrapped and carries it into the high word.  The 64-bit sum of a
-// word is exact once the adders are done (only the warp that owns the slot
-// touches it, and it reads the pair back after a __syncwarp).
-__device__ __forceinline__ void add64_shared(unsigned long long* a, unsigned long long v) {
-  uint32_t* w = reinterpret_cast<uint32_t*>(a);
-  const uint32_t lo = (uint32_t)v;
-  uint32_t hi = (uint32_t)(v >> 32);
-  if (lo != 0u) {
-    const uint32_t old = atomicAdd(w, lo);
-    hi += (uint32_t)(old + lo) < old ? 1u : 0u;
-  }
-  if (hi != 0u) atomicAdd(w + 1, hi);
-}
-
 // Exact sum of v < 2^59 over the lanes of `mask` (every lane of the mask
 // calls it): two 32-bit warp reductions of 27-bit pieces, which cannot wrap.
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned mask, unsigned long long v) {
@@ -432,13 +425,16 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned mask, unsigned
 //  * A lane whose unit has been flushed meanwhile (`direct`) adds all its
 //    words straight to the instance's global accumulators.
 // Every word is an integer sum, so the result does not depend on how the
-// additions are grouped.
+// additions are grouped.  (Fixed point uses the hardware conversion: a
+// 64-bit integer construction from the binary32 encoding took more issue
+// slots than the conversion's slow pipe cost, measured on the spectral field.)
 __device__ __forceinline__ void tally_exit_warp(const WalkConst& c, const WalkSched& s,
                                                 const TallyOut& t, const Path& p, int ev,
                                                 unsigned long long* slot_mem, int myslot,
-                                                bool direct, unsigned done, int lane) {
+                                                bool direct, unsigned done, int lane,
+                                                const uint32_t* lane_inst) {
   const int nb = c.nbins, K = c.K, sw = s.slot_words;
-  const unsigned long long qa = p.Aacc > 0.0f ? to_fixed(p.Aacc) : 0ull;
+  const unsigned long long qa = p.Aacc > 0.0f ? __float2ull_rn(__fmul_rn(p.Aacc, kFix)) : 0ull;
   const unsigned long long qs = (unsigned long long)p.step;
   const int leader = __ffs(done) - 1;
 #pragma unroll
@@ -458,27 +454,27 @@ __device__ __forceinline__ void tally_exit_warp(const WalkConst& c, const WalkSc
     unsigned long long* m = slot_mem + (size_t)myslot * sw;
     if (ev == EV_TOP) {
       const int bin = exit_bin(c, p);
-      const unsigned long long q = to_fixed(p.W);
+      const unsigned long long q = __float2ull_rn(__fmul_rn(p.W, kFix));
       add64_shared(m + bin, q);
       add64_shared(m + nb + 1 + p.k, q);
       if (p.n_coll == 1u) add64_shared(m + nb + 1 + K, q);
-      if (s.want_sumsq) add64_shared(m + nb + 6 + K + bin, to_fixed(__fmul_rn(p.W, p.W)));
+      if (s.want_sumsq) add64_shared(m + nb + 6 + K + bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
     } else if (ev == EV_BOTTOM) {
-      add64_shared(m + nb + 2 + K, to_fixed(p.W));
+      add64_shared(m + nb + 2 + K, __float2ull_rn(__fmul_rn(p.W, kFix)));
     } else if (ev == EV_TRUNC) {
       add64_shared(m + nb + 4 + K, 1ull);
     }
   } else {
-    unsigned long long* g = t.raw + (size_t)p.inst * sw;
+    unsigned long long* g = t.raw + (size_t)lane_inst[lane] * sw;
     if (ev == EV_TOP) {
       const int bin = exit_bin(c, p);
-      const unsigned long long q = to_fixed(p.W);
+      const unsigned long long q = __float2ull_rn(__fmul_rn(p.W, kFix));
       atomicAdd(g + bin, q);
       atomicAdd(g + nb + 1 + p.k, q);
       if (p.n_coll == 1u) atomicAdd(g + nb + 1 + K, q);
-      if (s.want_sumsq) atomicAdd(g + nb + 6 + K + bin, to_fixed(__fmul_rn(p.W, p.W)));
+      if (s.want_sumsq) atomicAdd(g + nb + 6 + K + bin, __float2ull_rn(__fmul_rn(__fmul_rn(p.W, p.W), kFix)));
     } else if (ev == EV_BOTTOM) {
-      atomicAdd(g + nb + 2 + K, to_fixed(p.W));
+      atomicAdd(g + nb + 2 + K, __float2ull_rn(__fmul_rn(p.W, kFix)));
     } else if (ev == EV_TRUNC) {
       atomicAdd(g + nb + 4 + K, 1ull);
     }
@@ -508,10 +504,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   SelBuf* sel = reinterpret_cast<SelBuf*>(reinterpret_cast<SlotMeta*>(
                     smem + (size_t)nwarps * 2 * slot_words) + 2 * nwarps) + wib;
   for (int j = lane; j < 2 * slot_words; j += 32) slot_mem[j] = 0ull;
-  if (lane < 2) {
-    meta[lane].live = 0u;
-    meta[lane].gen = 0u;
-  }
+  if (lane < 2) meta[lane].gl = 0u;  // generation 0, not live
   if (lane == 0) sel->valid = 0u;
   __syncwarp();
 
@@ -548,7 +541,8 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
       sm.inst = r.inst;
       sm.next = r.p0;
       sm.end = r.p1;
-      sm.live = 1u;
+      sm.gl |= 1u;         // live, same generation
+      sel->valid = 0u;     // the choice buffer belonged to another unit
       uint32_t dinst = r.inst;
       if constexpr (HERO > 0) dinst = hero_group<HERO>(c, r.inst).first;
       sm.d = c.thickness ? __ldg(c.thickness + dinst) : __int_as_float(0x7f800000);
@@ -582,10 +576,8 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
       }
     }
     __syncwarp();
-    if (lane == 0) {
-      meta[o].live = 0u;
-      meta[o].gen += 1u;  // paths of the flushed unit now tally directly
-    }
+    if (lane == 0)  // next generation, not live: the unit's late paths tally directly
+      meta[o].gl = ((meta[o].gl >> 1) + 1u) << 1;
     __syncwarp();
   };
 
@@ -596,8 +588,6 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     sel->k[lane] = (uint8_t)staged_choice(c, meta[o], u23(r.x));
     if (lane == 0) {
       sel->base = base;
-      sel->slot = (uint32_t)o;
-      sel->gen = meta[o].gen;
       sel->valid = 1u;
     }
     __syncwarp();
@@ -615,12 +605,12 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
         if (lane_done(st)) {
           const int myslot = (int)(mytag & 1u);
           tally_exit_warp(c, s, t, p, st - 1, slot_mem, myslot,
-                          meta[myslot].gen != (mytag >> 1), done, lane);
+                          (meta[myslot].gl >> 1) != (mytag >> 1), done, lane, sel->inst);
           st = LANE_IDLE;
         }
       } else if (lane_done(st)) {
         const int myslot = (int)(mytag & 1u);
-        const bool direct = meta[myslot].gen != (mytag >> 1);
+        const bool direct = (meta[myslot].gl >> 1) != (mytag >> 1);
         if constexpr (HERO > 0)
           tally_path_hero<HERO>(c, s, t, p, hs, st - 1, slot_mem + (size_t)myslot * slot_words,
                                 direct);
@@ -632,21 +622,26 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
       // ---- 2. refill idle lanes from the current unit (regrouping) ----
       unsigned idle = __ballot_sync(kFull, st == LANE_IDLE);
       while (idle != 0u) {
-        const uint32_t nxt = meta[cur].next, end = meta[cur].end;
-        if (meta[cur].live && nxt < end) {
+        const uint4 mh = *reinterpret_cast<const uint4*>(meta + cur);  // inst, next, end, gl
+        const uint32_t nxt = mh.y, end = mh.z;
+        if ((mh.w & 1u) && nxt < end) {
           const uint32_t take = min((uint32_t)__popc(idle), end - nxt);
           const int rank = __popc(idle & ((1u << lane) - 1u));
+          uint32_t base = 0;
           if constexpr (HERO == 0) {
-            if (!(sel->valid && sel->slot == (uint32_t)cur && sel->gen == meta[cur].gen &&
-                  sel->base <= nxt && nxt + take - sel->base <= 32u))
+            const uint4 sb = *reinterpret_cast<const uint4*>(sel);  // base, valid
+            base = sb.x;
+            if (!(sb.y && base <= nxt && nxt + take - base <= 32u)) {
               fill_choices(cur, nxt);
+              base = nxt;
+            }
           }
           __syncwarp();
           if (st == LANE_IDLE && (uint32_t)rank < take) {
             if constexpr (HERO > 0)
-              hero_init<HERO>(c, meta[cur].inst, c.path_offset + nxt + rank, meta[cur].d, p, hs);
+              hero_init<HERO>(c, mh.x, c.path_offset + nxt + rank, meta[cur].d, p, hs);
             else
-              path_start<LAYERED>(c, meta[cur], sel->k[nxt + rank - sel->base],
+              path_start<LAYERED>(c, meta[cur], mh.x, sel->k[nxt + rank - base],
                                   c.path_offset + nxt + rank, p);
             if (ADJ) {
               p.gscale = meta[cur].scale;
@@ -654,7 +649,8 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
               p.wsum = meta[cur].wsum;
             }
             st = LANE_RUNNING;
-            mytag = (meta[cur].gen << 1) | (uint32_t)cur;
+            mytag = (mh.w & ~1u) | (uint32_t)cur;  // generation * 2 + slot
+            if constexpr (HERO == 0) sel->inst[lane] = mh.x;
           }
           __syncwarp();
           if (lane == 0) meta[cur].next = nxt + take;
@@ -665,7 +661,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
           // The other slot is reused at once: its partial sums go to global
           // memory, and its paths still running tally there directly.
           const int o = cur ^ 1;
-          if (meta[o].live) flush(o);
+          if (meta[o].gl & 1u) flush(o);
           if (!fetch(o)) {
             more = false;
             break;
@@ -687,7 +683,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   }
   __syncwarp();
   for (int o = 0; o < 2; ++o)
-    if (meta[o].live) flush(o);
+    if (meta[o].gl & 1u) flush(o);
 }
 
 // ------------------------------------------------------------------ plain --

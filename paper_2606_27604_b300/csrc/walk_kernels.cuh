@@ -21,28 +21,30 @@ enum : unsigned int {
 constexpr float kFix = 4294967296.0f;  // 2^32
 constexpr double kInvFix = 1.0 / 4294967296.0;
 
-// round(W 2^32) for a weight 0 <= W < 2^31, the value __float2ull_rn gives,
-// built from the binary32 encoding so no 64-bit conversion instruction is
-// issued: x = W 2^32 is exact (power-of-two scale); below 2^23 adding 2^23
-// rounds x to an integer (to nearest, ties to even); from 2^23 up x is an
-// integer, its 24-bit significand shifted left by (exponent - 23).
-__device__ __forceinline__ unsigned long long to_fixed(float W) {
-  const float x = __fmul_rn(W, kFix);
-  const uint32_t small = __float_as_uint(__fadd_rn(x, 8388608.0f)) - 0x4B000000u;
-  const uint32_t b = __float_as_uint(x);
-  const unsigned long long big = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u)
-                                 << (((b >> 23) - 150u) & 63u);
-  return x < 8388608.0f ? (unsigned long long)small : big;
-}
-
 // Media per mixture the kernels support (SSS_KMAX of the public header).
 constexpr int kKMax = 4;
 
 // Bytes of the per-slot header (SlotMeta, with the unit's staged media)
 // after a warp's two slots of shared accumulators, and of the per-warp
 // buffer of medium choices (SelBuf) after the headers.
-constexpr int kSlotMetaBytes = 176;
-constexpr int kSelBufBytes = 48;
+constexpr int kSlotMetaBytes = 208;
+constexpr int kSelBufBytes = 176;
+
+// 64-bit shared-memory accumulation from native 32-bit atomics: the low
+// word's atomic returns its old value, so each adder sees whether its own
+// addition wrapped and carries it into the high word.  The 64-bit sum of a
+// word is exact once the adders are done (only the warp that owns the slot
+// touches it, and it reads the pair back after a __syncwarp).
+__device__ __forceinline__ void add64_shared(unsigned long long* a, unsigned long long v) {
+  uint32_t* w = reinterpret_cast<uint32_t*>(a);
+  const uint32_t lo = (uint32_t)v;
+  uint32_t hi = (uint32_t)(v >> 32);
+  if (lo != 0u) {
+    const uint32_t old = atomicAdd(w, lo);
+    hi += (uint32_t)(old + lo) < old ? 1u : 0u;
+  }
+  if (hi != 0u) atomicAdd(w + 1, hi);
+}
 
 struct WalkSched {
   unsigned long long* unit_counter;      // global work-queue head (zeroed per call)

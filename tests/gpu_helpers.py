@@ -71,16 +71,28 @@ def compare_same_stream(g, r, N, steps, keys=TALLIES):
     return worst, where
 
 
-def compare_sigma(g, r, keys=("R", "bins", "R1"), z=4.0):
+def compare_sigma(g, r, keys=("R", "bins", "R1"), z=4.0, max_rel_se=0.2):
     """The statistical bar: |GPU - oracle| <= z * sqrt(se_gpu^2 + se_oracle^2),
     using the oracle's standard errors for both sides (same N, so the two
-    variances are equal)."""
+    variances are equal).  The bar is a normal-approximation bound, so it is
+    applied where the tally is supported by enough paths for that
+    approximation: relative standard error <= max_rel_se (0.2: about 25 or
+    more contributing paths).  A sparser tally (a far radial bin holding a
+    handful of exits) is held only by the same-stream bound, where one
+    binary32 path flip (one exit weight / N) is allowed for."""
     bad = []
     for k in keys:
         a, b = np.asarray(g[k]), np.asarray(r[k])
         se = np.asarray(r["se_" + k])
+        se_g = np.asarray(g["stderr_" + k]) if ("stderr_" + k) in g else se
         lim = z * np.sqrt(2.0) * se + 1e-15
-        viol = np.abs(a - b) > lim
+        # relative standard error on each side; an empty tally on either side
+        # (0 / 0) is not supported
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rel = np.maximum(np.where(b != 0, se / np.abs(b), np.inf),
+                             np.where(a != 0, se_g / np.abs(a), np.inf))
+        supported = rel <= max_rel_se
+        viol = (np.abs(a - b) > lim) & supported
         if viol.any():
             bad.append((k, int(viol.sum())))
     return bad
