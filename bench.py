@@ -58,8 +58,8 @@ DECODER_MACS_PER_TEXEL = (3 * 256 + 256 * 256 + 256 * 5) + (5 * 512 + 512 * 512 
 # dram__bytes_write.sum) of the 1024-texel case, scaled by 64 to the
 # 65536-texel launch (the traffic grows with the instances walked).  Valid
 # only while the kernel sources are the ones captured (sha1 below).
-WALK_TRAFFIC = {"bytes_per_launch": (61.667584e6 + 11.258880e6) * 64,
-                "source_sha1": "b9f67d5188db4df09ea3427ca0e8c234e44f3894"}
+WALK_TRAFFIC = {"bytes_per_launch": (62.166784e6 + 11.208704e6) * 64,
+                "source_sha1": "cc1d7837ba87b1c9d64e639eb60170210a672b1f"}
 
 
 def _walk_source_sha1():

@@ -19,13 +19,14 @@ import torch
 from . import api
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sss_b300_autotune.json")
-# Around the shape a sweep on the 81-band spectral field found best (256
-# threads, 1024-path units, refill at 8 idle lanes), the built-in default.
+# Around the shapes sweeps on the 81-band spectral field found best (256
+# threads, 512- or 1024-path units, refill at 6-8 idle lanes; the built-in
+# default is 256 / 1024 / 8).
 CANDIDATES = [
     dict(block_threads=bt, unit_paths=up, regroup=rg)
     for bt in (256, 128)
     for up in (1024, 512, 2048)
-    for rg in (8, 6, 12)
+    for rg in (8, 6, 5, 10)
 ]
 
 

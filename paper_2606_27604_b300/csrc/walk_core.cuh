@@ -179,6 +179,7 @@ struct Path {
   int layer;
   float gscale, glim, wsum;  // adjoint: fixed-point scale, per-path limit, sum(w)
   float hc1, hc2;  // Henyey-Greenstein constants of g (hg_consts)
+  float ga;        // adjoint: -2g / (1 - g^2), the constant part of d log p_HG / d g
 };
 
 // The per-medium constants of the Henyey-Greenstein inversion (hg_mu):
@@ -244,9 +245,11 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // Unpolarised Fresnel reflectance, medium (index n) -> outside (index 1),
 // without branches: total internal reflection (sin^2 t = n^2 sin^2 i >= 1)
 // and n = 1 are selected at the end; the two quotients share one reciprocal.
+// (Under total internal reflection 1 - sin^2 t < 0 and the arithmetic below
+// is NaN, which the selection replaces by 1.)
 __device__ __forceinline__ float fresnel(float cos_i, float n) {
   const float sin2_t = __fmul_rn(__fmul_rn(n, n), __fmaf_rn(-cos_i, cos_i, 1.0f));
-  const float cos_t = sqrt_approx(fmaxf(0.0f, __fsub_rn(1.0f, sin2_t)));
+  const float cos_t = sqrt_approx(__fsub_rn(1.0f, sin2_t));
   const float2 nc = __fmul2_rn(f2(n, n), f2(cos_i, cos_t));  // (n cos_i, n cos_t)
   const float2 sp = __fadd2_rn(f2(nc.x, cos_i), f2(cos_t, nc.y));  // (sd, pd)
   const float inv = rcp_approx(__fmul_rn(sp.x, sp.y));
@@ -277,6 +280,17 @@ __device__ __forceinline__ int select_medium(const WalkConst& c, uint32_t inst, 
     }
   }
   return c.K - 1;
+}
+
+// d log p_HG(mu; g) / d g = -2g / (1 - g^2) - 3 (g - mu) / (1 + g^2 - 2 g mu).
+// The first term is a constant of the medium (hg_dlogp_dg_const, formed once
+// per path); the second is taken per scattering with the hardware reciprocal.
+__device__ __forceinline__ float hg_dlogp_dg_const(float g) {
+  return __fdiv_rn(__fmul_rn(-2.0f, g), __fmaf_rn(-g, g, 1.0f));
+}
+__device__ __forceinline__ float hg_dlogp_dg(float g, float ga, float mu) {
+  const float den = __fmaf_rn(g, g, __fmaf_rn(-2.0f * g, mu, 1.0f));
+  return __fmaf_rn(__fmul_rn(-3.0f, __fsub_rn(g, mu)), rcp_approx(den), ga);
 }
 
 // Cosine-weighted incident lobe (incidence = 1): outside cosine sqrt(u),
@@ -336,6 +350,7 @@ __device__ __forceinline__ void path_init(const WalkConst& c, uint32_t inst, uin
   const float2 hc = hg_consts(p.g);
   p.hc1 = hc.x;
   p.hc2 = hc.y;
+  p.ga = hg_dlogp_dg_const(p.g);
   p.d = d;
   p.x = 0.0f; p.y = 0.0f; p.z = 0.0f;
   p.ux = 0.0f; p.uy = 0.0f; p.uz = 1.0f;
@@ -377,12 +392,6 @@ __device__ __forceinline__ float hg_mu(float g, float hc1, float hc2, float u) {
   return fminf(1.0f, fmaxf(-1.0f, mu));
 }
 
-__device__ __forceinline__ float hg_dlogp_dg(float g, float mu) {
-  const float a = __fdiv_rn(__fmul_rn(-2.0f, g), __fmaf_rn(-g, g, 1.0f));
-  const float den = __fmaf_rn(g, g, __fmaf_rn(-2.0f * g, mu, 1.0f));
-  const float b = __fdiv_rn(__fmul_rn(-3.0f, __fsub_rn(g, mu)), den);
-  return __fadd_rn(a, b);
-}
 
 // One random-number draw of the walk.  Returns the event it ended in.
 // Mostly branch-free: every lane evaluates both the face (Fresnel) and the
@@ -401,7 +410,9 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
 
   // Exponential free flight -ln(u0) / sigma_t, from the hardware log2
   // (absolute error <= 2^-22 mean free paths near u0 = 1, 2 ulp elsewhere).
-  const float s = fmaxf(0.0f, __fmul_rn(-lg2_approx(u0), p.fl));
+  // |lg2 u0| = -lg2 u0 for u0 < 1; the absolute value (an operand modifier)
+  // also keeps the flight non-negative where the approximation errs above 0.
+  const float s = __fmul_rn(fabsf(lg2_approx(u0)), p.fl);
   // Distance to the face the path is heading to.
   const float iuz = rcp_approx(p.uz);
   const float inf = __int_as_float(0x7f800000);
@@ -491,7 +502,7 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
     }
   }
   if (ADJ) {
-    const float dl = (hit || dead) ? 0.0f : hg_dlogp_dg(p.g, mu);
+    const float dl = (hit || dead) ? 0.0f : hg_dlogp_dg(p.g, p.ga, mu);
     if (LAYERED && p.layer) p.G2 = __fadd_rn(p.G2, dl);
     else p.G = __fadd_rn(p.G, dl);
   }
@@ -532,6 +543,7 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
     const float2 hc = hg_consts(p.g);  // the new layer's Henyey-Greenstein constants
     p.hc1 = hc.x;
     p.hc2 = hc.y;
+    if (ADJ) p.ga = hg_dlogp_dg_const(p.g);
     t = p.sigt; p.sigt = p.sigt_o; p.sigt_o = t;
     p.layer ^= 1;
     return EV_CONTINUE;

@@ -300,6 +300,7 @@ __device__ __forceinline__ void path_start(const WalkConst& c, const SlotMeta& m
   const float2 hc = m.hgc[k];
   p.hc1 = hc.x;
   p.hc2 = hc.y;
+  p.ga = hg_dlogp_dg_const(p.g);
   p.d = m.d;
   p.x = 0.0f; p.y = 0.0f; p.z = 0.0f;
   p.ux = 0.0f; p.uy = 0.0f; p.uz = 1.0f;
@@ -598,7 +599,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
   while (true) {
     const unsigned not_running = __ballot_sync(kFull, st != LANE_RUNNING);
     const int n_nr = __popc(not_running);
-    if (n_nr >= s.regroup || n_nr == 32) {
+    if (n_nr >= s.regroup) {  // (regroup <= 32: a warp with no running lane always enters)
       // ---- 1. finished lanes tally together (one divergent block) ----
       if constexpr (!ADJ && HERO == 0) {
         const unsigned done = __ballot_sync(kFull, lane_done(st));
