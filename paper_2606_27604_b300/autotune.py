@@ -64,7 +64,7 @@ def _time(m: api.Media, o: api.WalkOptions, reps: int) -> float:
     return a.elapsed_time(b) / reps
 
 
-def tune(m: api.Media, o: api.WalkOptions, max_inst: int = 1 << 15, reps: int = 2,
+def tune(m: api.Media, o: api.WalkOptions, max_inst: int = 1 << 17, reps: int = 3,
          cache_path: Optional[str] = DEFAULT_CACHE, candidates=CANDIDATES) -> api.WalkOptions:
     """Returns `o` with the fastest launch shape for this workload."""
     key = _key(m, o)

@@ -540,7 +540,7 @@ cudaError_t launch_gemm(int bn, int epi, const CUtensorMap& ta, const CUtensorMa
                         const EpiParams& ep, unsigned int* status, cudaStream_t st) {
 #define SSS_GEMM(BN_, EPI_) \
   return launch_gemm_t<BN_, EPI_>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st)
-  if (epi == EPI_FINAL && bn == 144) SSS_GEMM(144, EPI_FINAL);
+  if (epi == EPI_FINAL && bn == kFinalBN) SSS_GEMM(kFinalBN, EPI_FINAL);
   if (epi == EPI_HIDDEN) {
     switch (bn) {
       case 16: SSS_GEMM(16, EPI_HIDDEN);

@@ -17,15 +17,22 @@ enum : unsigned int { DEC_FLAG_TIMEOUT = 0x10u };
 // Dec_T's last layer, grouped for the epilogue: 41 groups of 36 rows (the
 // source band of even visible band 2P, then the two source bands around odd
 // visible band 2P+1, each 12 rows = 3 media x (alpha, g, sigma_t, w)),
-// padded to 11 tiles of 144 rows.  Visible band j (380 + 5j nm) sits at
+// packed 7 groups (252 rows + 4 padding rows) to a 256-row tile: 6 tiles,
+// so each 128-row block of activations is read 6 times per layer instead of
+// the 11 times of 144-row tiles.  Visible band j (380 + 5j nm) sits at
 // source index 65 + 2.5 j on the 250-1000 nm, 2 nm grid.
 constexpr int kDstBands = 81;
 constexpr int kPairs = 41;
-constexpr int kFinalBN = 144;
-constexpr int kFinalRows = 11 * kFinalBN;  // 1584
+constexpr int kFinalBN = 256;
+constexpr int kGroupsPerTile = kFinalBN / 36;                            // 7
+constexpr int kFinalTiles = (kPairs + kGroupsPerTile - 1) / kGroupsPerTile;  // 6
+constexpr int kFinalRows = kFinalTiles * kFinalBN;                       // 1536
 
 __host__ __device__ inline int dect_out_source_row(int r) {
-  const int P = r / 36, rem = r % 36, slot = rem / 12, within = rem % 12;
+  const int tile = r / kFinalBN, in_tile = r % kFinalBN;
+  if (in_tile >= kGroupsPerTile * 36) return -1;  // padding rows of a tile
+  const int P = tile * kGroupsPerTile + in_tile / 36, rem = in_tile % 36;
+  const int slot = rem / 12, within = rem % 12;
   if (P >= kPairs) return -1;
   const int s = 65 + 5 * P + (slot == 0 ? 0 : (slot == 1 ? 2 : 3));
   return s * 12 + within;
