@@ -266,31 +266,35 @@ def run_pipeline(args):
     return 0
 
 
-def run_lut(args):
+def lut_leg(n, n_paths):
     """Scale-independent LUT precompute (one instance per (alpha, g) grid
-    point, sigma_t = 1, K = 1), timed on the GPU."""
+    point, sigma_t = 1, K = 1), timed on the GPU, with the time the paper's
+    800 x 800 x 10^6-path table would take at the same rate."""
     import torch
     from paper_2606_27604_b300 import lut
-    n = args.lut_side
     alphas = np.linspace(0.0, 0.999, n)
     gs = np.linspace(0.0, 0.95, n)
     lut.build(alphas[:8], gs[:8], n_paths=1024, nbins=128)   # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    L = lut.build(alphas, gs, n_paths=args.lut_paths, nbins=128, r_max=32.0)
+    L = lut.build(alphas, gs, n_paths=n_paths, nbins=128, r_max=32.0)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    paths = float(n * n) * args.lut_paths
-    line = {"metric": "LUT precompute paths/s (Sec. 4.2 tables R(alpha,g), P_d(r|alpha,g))",
-            "workload": f"{n}x{n} (alpha, g) grid x {args.lut_paths} paths, 128 bins to 32 mfp, "
-                        "n=1.4", "seconds": dt, "paths_per_s": paths / dt,
+    paths = float(n * n) * n_paths
+    return {"workload": f"{n}x{n} (alpha, g) grid x {n_paths} paths, 128 bins to 32 mfp, n=1.4",
+            "seconds": dt, "paths_per_s": paths / dt,
             "full_paper_table_estimate_s": 800 * 800 * 1e6 / (paths / dt),
             "R_range": [float(L.R.min()), float(L.R.max())]}
+
+
+def run_lut(args):
+    line = dict(metric="LUT precompute paths/s (Sec. 4.2 tables R(alpha,g), P_d(r|alpha,g))",
+                **lut_leg(args.lut_side, args.lut_paths))
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_fit(args):
+def fit_leg(n, steps):
     """Batched LUT mixture fit (Sec. 4.2): K = 3, Adam, timed on the GPU and
     extrapolated to the paper's 25,000 tones x 376 bands x 10,000 steps."""
     import torch
@@ -301,7 +305,7 @@ def run_fit(args):
     L = lut.build(alphas, gs, n_paths=1 << 14, nbins=64, r_max=32.0)
     dens = torch.from_numpy(L.density().astype(np.float32)).to(dev)
     Rl = torch.from_numpy(L.R.astype(np.float32)).to(dev)
-    n, K, steps = args.fit_problems, 3, args.fit_steps
+    K = 3
     rng = np.random.default_rng(0)
     r = torch.from_numpy(np.linspace(0.05, 4.0, 64).astype(np.float32)).to(dev)
     lam = rng.uniform(0.5, 3.0, size=(n, 1))
@@ -321,12 +325,16 @@ def run_fit(args):
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) / 1e3
     rate = n * steps / sec
-    line = {"metric": "LUT mixture fit problem-steps/s (K=3, 64 radii, Adam)",
-            "workload": f"{n} problems x {steps} steps, 64x32x64 table", "seconds": sec,
+    return {"workload": f"{n} problems x {steps} steps, 64x32x64 table", "seconds": sec,
             "problem_steps_per_s": rate,
             "paper_workload_estimate_s": 25000 * 376 * 10000 / rate,
             "paper_workload_paper_time_s": 46 * 3600,
             "median_final_loss": float(loss.median().item())}
+
+
+def run_fit(args):
+    line = dict(metric="LUT mixture fit problem-steps/s (K=3, 64 radii, Adam)",
+                **fit_leg(args.fit_problems, args.fit_steps))
     print(json.dumps(line), flush=True)
     return 0
 
@@ -378,6 +386,8 @@ def main():
                     help="skip the full-pipeline leg of the default line")
     ap.add_argument("--pipeline-side", type=int, default=1024)
     ap.add_argument("--lut", action="store_true", help="time the LUT precompute instead")
+    ap.add_argument("--no-lut", action="store_true",
+                    help="skip the LUT precompute and LUT fit legs of the default line")
     ap.add_argument("--lut-side", type=int, default=128)
     ap.add_argument("--lut-paths", type=int, default=1 << 20)
     ap.add_argument("--fit", action="store_true", help="time the batched LUT fit instead")
@@ -696,6 +706,12 @@ def main():
     if not args.no_pipeline and ws == 1:
         pipeline = pipeline_leg(side=args.pipeline_side)
 
+    # ---- LUT precompute and LUT mixture fit (Sec. 4.2), bounded sizes -------
+    lut_res = fit_res = None
+    if not args.no_lut and ws == 1:
+        lut_res = lut_leg(128, 1 << 16)
+        fit_res = fit_leg(1 << 16, 1000)
+
     # ---- roofline of the walk kernel --------------------------------------
     kmean = float(np.mean(kern))
     f_mhz = clk["sm_mhz"] if clk else 2032.0
@@ -764,7 +780,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu,
             "adjoint_forward_ratio": ratio, "baselines": baselines, "hero_wavelength": hero,
             "probe": probe,
-            "decoder": decoder, "pipeline": pipeline,
+            "decoder": decoder, "pipeline": pipeline, "lut": lut_res, "lut_fit": fit_res,
             "launch_shape": dict({k: getattr(o, k) for k in ("block_threads", "unit_paths",
                                                              "regroup")},
                                  autotuned=not args.no_autotune, cuda_graph=bool(o.use_graph)),

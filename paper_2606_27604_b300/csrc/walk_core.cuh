@@ -247,7 +247,8 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // and n = 1 are selected at the end; the two quotients share one reciprocal.
 // (Under total internal reflection 1 - sin^2 t < 0 and the arithmetic below
 // is NaN, which the selection replaces by 1.)
-__device__ __forceinline__ float fresnel(float cos_i, float n) {
+// fresnel_parts: sin^2 t and the reflectance without the two selections.
+__device__ __forceinline__ float fresnel_parts(float cos_i, float n, float* sin2_t_out) {
   const float sin2_t = __fmul_rn(__fmul_rn(n, n), __fmaf_rn(-cos_i, cos_i, 1.0f));
   const float cos_t = sqrt_approx(__fsub_rn(1.0f, sin2_t));
   const float2 nc = __fmul2_rn(f2(n, n), f2(cos_i, cos_t));  // (n cos_i, n cos_t)
@@ -256,9 +257,23 @@ __device__ __forceinline__ float fresnel(float cos_i, float n) {
   const float2 df = __fadd2_rn(f2(nc.x, cos_i), f2(-cos_t, -nc.y));
   const float2 rr = __fmul2_rn(__fmul2_rn(df, f2(sp.y, sp.x)), f2(inv, inv));
   const float rs = rr.x, rp = rr.y;
-  float F = __fmul_rn(0.5f, __fmaf_rn(rs, rs, __fmul_rn(rp, rp)));
+  *sin2_t_out = sin2_t;
+  return __fmul_rn(0.5f, __fmaf_rn(rs, rs, __fmul_rn(rp, rp)));
+}
+__device__ __forceinline__ float fresnel(float cos_i, float n) {
+  float sin2_t;
+  float F = fresnel_parts(cos_i, n, &sin2_t);
   F = sin2_t >= 1.0f ? 1.0f : F;
   return n == 1.0f ? 0.0f : F;
+}
+// The reflect-or-leave choice at a face, u < fresnel(cos_i, n), taken with
+// predicates instead of the two selections: total internal reflection always
+// reflects, n = 1 never does (cos_i = 0, where the two forms would differ for
+// n = 1, never reaches a face).
+__device__ __forceinline__ bool fresnel_reflects(float cos_i, float n, float u) {
+  float sin2_t;
+  const float F = fresnel_parts(cos_i, n, &sin2_t);
+  return sin2_t >= 1.0f || (n != 1.0f && u < F);
 }
 
 // Medium choice: first k whose running binary32 CDF of w/sum(w) exceeds u.
@@ -444,8 +459,7 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
   }
 
   // Face: smooth-dielectric Fresnel, reflect with probability F.
-  const float F = fresnel(fabsf(p.uz), c.n_rel);
-  const bool reflect = hit && !cross && (u1 < F);
+  const bool reflect = hit && !cross && fresnel_reflects(fabsf(p.uz), c.n_rel, u1);
 
   // Collision: albedo weighting with roulette, or analog absorption.
   bool dead;
