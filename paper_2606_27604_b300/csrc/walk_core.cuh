@@ -408,11 +408,44 @@ __device__ __forceinline__ float hg_mu(float g, float hc1, float hc2, float u) {
 }
 
 
+// New direction after a scattering with cosine mu and azimuth phi = 2 pi u:
+// the standard frame rotation of (ux, uy, uz), with the pole |uz| ~ 1 taken
+// in the fixed frame, renormalised.  phi is evaluated as phi - pi in
+// (-pi, pi) and the sine and cosine negated.
+__device__ __forceinline__ void scatter_direction(Path& p, float mu, float u) {
+  float sp, cp;
+  sincos_approx(__fmaf_rn(u, 6.2831853071795865f, -3.14159265358979324f), &sp, &cp);
+  sp = -sp;
+  cp = -cp;
+  // mu is clamped to [-1, 1], so 1 - mu^2 (one rounding) is never negative
+  const float st = sqrt_approx(__fmaf_rn(-mu, mu, 1.0f));
+  const float s2 = __fmaf_rn(-p.uz, p.uz, 1.0f);
+  const float itmp = rsqrt_approx(s2);
+  const float2 ts = __fmul2_rn(make_float2(s2, st), make_float2(itmp, itmp));
+  const float tmp = ts.x, sti = ts.y;
+  const float uzcp = __fmul_rn(p.uz, cp);
+  const bool polar = fabsf(p.uz) > 0.999999f;
+  // (nx, ny) off the pole: sti (u_xy uz cp -+ u_yx sp) + u_xy mu, in pairs
+  const float2 cross_sp = __fmul2_rn(f2(-p.uy, p.ux), f2(sp, sp));
+  const float2 inner = __ffma2_rn(f2(p.ux, p.uy), f2(uzcp, uzcp), cross_sp);
+  const float2 nxy = __ffma2_rn(f2(sti, sti), inner, __fmul2_rn(f2(p.ux, p.uy), f2(mu, mu)));
+  const float2 pxy = __fmul2_rn(f2(st, st), f2(cp, sp));
+  const float nx = polar ? pxy.x : nxy.x;
+  const float ny = polar ? pxy.y : nxy.y;
+  const float nz = polar ? (p.uz >= 0.0f ? mu : -mu)
+                         : __fmaf_rn(-pxy.x, tmp, __fmul_rn(p.uz, mu));
+  const float inr = rsqrt_approx(__fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz))));
+  const float2 uxy = __fmul2_rn(f2(nx, ny), f2(inr, inr));
+  p.ux = uxy.x;
+  p.uy = uxy.y;
+  p.uz = __fmul_rn(nz, inr);
+}
+
 // One random-number draw of the walk.  Returns the event it ended in.
-// Mostly branch-free: every lane evaluates both the face (Fresnel) and the
-// collision (weighting, Henyey-Greenstein, rotation) arithmetic and selects
-// the outcome of the event it actually met, so lanes of a warp that meet
-// different events issue the same instructions.  SEMI = true compiles the
+// The flight and face test are common; the face (Fresnel) and the collision
+// (weighting, Henyey-Greenstein, rotation) are then two branches, so a warp
+// runs each with the lanes that met that event (hero-wavelength groups
+// evaluate both and select).  SEMI = true compiles the
 // semi-infinite slab (no far face: p.d is +inf), where only the entry face
 // can be met; the results are those of the general form for d = +inf.
 template <bool ADJ, bool LAYERED = false, int HERO = 0, bool SEMI = false>
@@ -458,54 +491,72 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
     else p.L = __fadd_rn(p.L, dist);
   }
 
-  // Face: smooth-dielectric Fresnel, reflect with probability F.
-  const bool reflect = hit && !cross && fresnel_reflects(fabsf(p.uz), c.n_rel, u1);
-
-  // Collision: albedo weighting with roulette, or analog absorption.
-  bool dead;
-  if (c.mode == 0) {
-    // the surviving weight W alpha and the deposit W - W alpha (one rounding)
+  bool reflect = false, dead = false;
+  if constexpr (HERO <= 1) {
+    // One path per band: the face and the collision are separate branches,
+    // so each lane runs only the arithmetic of the event it met.
+    if (hit) {
+      // Face: smooth-dielectric Fresnel, reflect with probability F.
+      reflect = !cross && fresnel_reflects(fabsf(p.uz), c.n_rel, u1);
+      if (reflect) p.uz = -p.uz;
+    } else {
+      // Collision: albedo weighting with roulette, or analog absorption.
+      if (c.mode == 0) {
+        // the surviving weight W alpha and the deposit W - W alpha (one rounding)
+        const float Wn = __fmul_rn(p.W, p.alpha);
+        const float An = __fadd_rn(__fmaf_rn(p.W, -p.alpha, p.W), p.Aacc);
+        const bool low = Wn < c.rr_th;
+        dead = low && !(u3 < __fmul_rn(Wn, c.inv_rr_th));
+        p.W = low ? c.rr_th : Wn;
+        p.Aacc = An;
+      } else {
+        dead = u3 >= p.alpha;
+        p.Aacc = dead ? __fadd_rn(p.Aacc, p.W) : p.Aacc;
+      }
+      p.n_coll += 1u;
+      if (ADJ && LAYERED) p.n2 += p.layer ? 1u : 0u;
+      // Henyey-Greenstein scattering with this medium's g.
+      const float mu = hg_mu(p.g, p.hc1, p.hc2, u1);
+      if (ADJ) {
+        const float dl = dead ? 0.0f : hg_dlogp_dg(p.g, p.ga, mu);
+        if (LAYERED && p.layer) p.G2 = __fadd_rn(p.G2, dl);
+        else p.G = __fadd_rn(p.G, dl);
+      }
+      scatter_direction(p, mu, u2);
+    }
+  } else {
+    // Hero-wavelength members (HERO = C > 1): every lane evaluates both the
+    // face and the collision arithmetic and selects, since the members'
+    // density ratios take terms from both.
+    reflect = hit && !cross && fresnel_reflects(fabsf(p.uz), c.n_rel, u1);
+    // collision: the members' flight density exp(-sigma dist), and on a
+    // collision sigma and the albedo.  Roulette is decided on the largest
+    // member weight Wr and boosts every member by rr_th / Wr.
     const float Wn = __fmul_rn(p.W, p.alpha);
     const float An = __fadd_rn(__fmaf_rn(p.W, -p.alpha, p.W), p.Aacc);
-    if constexpr (HERO <= 1) {
-      const bool low = Wn < c.rr_th;
-      dead = !hit && low && !(u3 < __fmul_rn(Wn, c.inv_rr_th));
-      p.W = hit ? p.W : (low ? c.rr_th : Wn);
-    } else {
-      // hero-wavelength members: flight density exp(-sigma dist), and on a
-      // collision sigma and the albedo.  Roulette is decided on the largest
-      // member weight Wr and boosts every member by rr_th / Wr.
-      const float coll = hit ? 0.0f : 1.0f;
-      float Wm[HERO > 1 ? HERO - 1 : 1];
-      float Wr = Wn;
+    const float coll = hit ? 0.0f : 1.0f;
+    float Wm[HERO > 1 ? HERO - 1 : 1];
+    float Wr = Wn;
 #pragma unroll
-      for (int m = 0; m < HERO - 1; ++m) {
-        hs.D[m] = __fmaf_rn(coll, hs.ls[m], __fmaf_rn(hs.ds[m], dist, hs.D[m]));
-        Wm[m] = __fmul_rn(hs.W[m], hs.a[m]);
-        Wr = fmaxf(Wr, Wm[m]);
-      }
-      const bool low = Wr < c.rr_th;
-      dead = !hit && low && !(u3 < __fmul_rn(Wr, c.inv_rr_th));
-      const float boost = __fmul_rn(c.rr_th, rcp_approx(Wr));
-      p.W = hit ? p.W : (low ? (Wn == Wr ? c.rr_th : __fmul_rn(Wn, boost)) : Wn);
-#pragma unroll
-      for (int m = 0; m < HERO - 1; ++m)
-        hs.W[m] = hit ? hs.W[m]
-                      : (low ? (Wm[m] == Wr ? c.rr_th : __fmul_rn(Wm[m], boost)) : Wm[m]);
+    for (int m = 0; m < HERO - 1; ++m) {
+      hs.D[m] = __fmaf_rn(coll, hs.ls[m], __fmaf_rn(hs.ds[m], dist, hs.D[m]));
+      Wm[m] = __fmul_rn(hs.W[m], hs.a[m]);
+      Wr = fmaxf(Wr, Wm[m]);
     }
+    const bool low = Wr < c.rr_th;
+    dead = !hit && low && !(u3 < __fmul_rn(Wr, c.inv_rr_th));
+    const float boost = __fmul_rn(c.rr_th, rcp_approx(Wr));
+    p.W = hit ? p.W : (low ? (Wn == Wr ? c.rr_th : __fmul_rn(Wn, boost)) : Wn);
+#pragma unroll
+    for (int m = 0; m < HERO - 1; ++m)
+      hs.W[m] = hit ? hs.W[m]
+                    : (low ? (Wm[m] == Wr ? c.rr_th : __fmul_rn(Wm[m], boost)) : Wm[m]);
     p.Aacc = hit ? p.Aacc : An;
-  } else {
-    dead = !hit && (u3 >= p.alpha);
-    p.Aacc = dead ? __fadd_rn(p.Aacc, p.W) : p.Aacc;
-  }
-  p.n_coll += hit ? 0u : 1u;
-  if (ADJ && LAYERED) p.n2 += (hit || !p.layer) ? 0u : 1u;
-
-  // Henyey-Greenstein scattering with this medium's g.
-  const float mu = hg_mu(p.g, p.hc1, p.hc2, u1);
-  if constexpr (HERO > 1) {
-    // log2 p_HG(mu; g_m) - log2 p_HG(mu; g_h)
+    p.n_coll += hit ? 0u : 1u;
+    // Henyey-Greenstein scattering with the hero's g, and the members'
+    //   log2 p_HG(mu; g_m) - log2 p_HG(mu; g_h)
     //   = log2((1-g_m^2)/(1-g_h^2)) - 1.5 (log2(1+g_m^2-2 g_m mu) - log2(1+g_h^2-2 g_h mu))
+    const float mu = hg_mu(p.g, p.hc1, p.hc2, u1);
     const float scat = (hit || dead) ? 0.0f : 1.0f;
     const float lh = lg2_approx(__fmaf_rn(__fmul_rn(-2.0f, p.g), mu, __fmaf_rn(p.g, p.g, 1.0f)));
 #pragma unroll
@@ -514,40 +565,12 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
       const float lm = lg2_approx(__fmaf_rn(__fmul_rn(-2.0f, gm), mu, __fmaf_rn(gm, gm, 1.0f)));
       hs.D[m] = __fmaf_rn(scat, __fmaf_rn(-1.5f, __fsub_rn(lm, lh), hs.cg[m]), hs.D[m]);
     }
+    const float ux0 = p.ux, uy0 = p.uy, uz0 = p.uz;
+    scatter_direction(p, mu, u2);
+    p.ux = hit ? ux0 : p.ux;
+    p.uy = hit ? uy0 : p.uy;
+    p.uz = hit ? (reflect ? -uz0 : uz0) : p.uz;
   }
-  if (ADJ) {
-    const float dl = (hit || dead) ? 0.0f : hg_dlogp_dg(p.g, p.ga, mu);
-    if (LAYERED && p.layer) p.G2 = __fadd_rn(p.G2, dl);
-    else p.G = __fadd_rn(p.G, dl);
-  }
-  // Azimuth phi = 2 pi u2; evaluated as phi - pi in (-pi, pi), then negated.
-  float sp, cp;
-  sincos_approx(__fmaf_rn(u2, 6.2831853071795865f, -3.14159265358979324f), &sp, &cp);
-  sp = -sp;
-  cp = -cp;
-  // mu is clamped to [-1, 1], so 1 - mu^2 (one rounding) is never negative
-  const float st = sqrt_approx(__fmaf_rn(-mu, mu, 1.0f));
-  const float s2 = __fmaf_rn(-p.uz, p.uz, 1.0f);
-  const float itmp = rsqrt_approx(s2);
-  const float2 ts = __fmul2_rn(make_float2(s2, st), make_float2(itmp, itmp));
-  const float tmp = ts.x, sti = ts.y;
-  const float uzcp = __fmul_rn(p.uz, cp);
-  const bool polar = fabsf(p.uz) > 0.999999f;
-  // (nx, ny) off the pole: sti (u_xy uz cp -+ u_yx sp) + u_xy mu, in pairs
-  const float2 cross_sp = __fmul2_rn(f2(-p.uy, p.ux), f2(sp, sp));
-  const float2 inner = __ffma2_rn(f2(p.ux, p.uy), f2(uzcp, uzcp), cross_sp);
-  const float2 nxy = __ffma2_rn(f2(sti, sti), inner, __fmul2_rn(f2(p.ux, p.uy), f2(mu, mu)));
-  const float2 pxy = __fmul2_rn(f2(st, st), f2(cp, sp));
-  const float nx = polar ? pxy.x : nxy.x;
-  const float ny = polar ? pxy.y : nxy.y;
-  const float nz = polar ? (p.uz >= 0.0f ? mu : -mu)
-                         : __fmaf_rn(-pxy.x, tmp, __fmul_rn(p.uz, mu));
-  const float inr = rsqrt_approx(__fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz))));
-  const float2 uxy = __fmul2_rn(f2(nx, ny), f2(inr, inr));
-  const float uz_new = hit ? (reflect ? -p.uz : p.uz) : __fmul_rn(nz, inr);
-  p.ux = hit ? p.ux : uxy.x;
-  p.uy = hit ? p.uy : uxy.y;
-  p.uz = uz_new;
 
   if (LAYERED && cross) {  // continue in the other layer with a fresh flight
     float t;
