@@ -444,8 +444,7 @@ __device__ __forceinline__ void scatter_direction(Path& p, float mu, float u) {
 // One random-number draw of the walk.  Returns the event it ended in.
 // The flight and face test are common; the face (Fresnel) and the collision
 // (weighting, Henyey-Greenstein, rotation) are then two branches, so a warp
-// runs each with the lanes that met that event (hero-wavelength groups
-// evaluate both and select).  SEMI = true compiles the
+// runs each with the lanes that met that event.  SEMI = true compiles the
 // semi-infinite slab (no far face: p.d is +inf), where only the entry face
 // can be met; the results are those of the general form for d = +inf.
 template <bool ADJ, bool LAYERED = false, int HERO = 0, bool SEMI = false>
@@ -484,8 +483,8 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
   const float2 xy = __ffma2_rn(f2(dist, dist), f2(p.ux, p.uy), f2(p.x, p.y));
   p.x = xy.x;
   p.y = xy.y;
-  if (SEMI) p.z = hit ? 0.0f : __fmaf_rn(dist, p.uz, p.z);  // a face hit is the top face
-  else p.z = hit ? (cross ? p.d1 : (top ? 0.0f : p.d)) : __fmaf_rn(dist, p.uz, p.z);
+  // the plane reached at a face (a semi-infinite slab has only the top face)
+  const float zface = SEMI ? 0.0f : (cross ? p.d1 : (top ? 0.0f : p.d));
   if (ADJ) {
     if (LAYERED && p.layer) p.L2 = __fadd_rn(p.L2, dist);
     else p.L = __fadd_rn(p.L, dist);
@@ -493,13 +492,15 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
 
   bool reflect = false, dead = false;
   if constexpr (HERO <= 1) {
-    // One path per band: the face and the collision are separate branches,
-    // so each lane runs only the arithmetic of the event it met.
+    // The face and the collision are separate branches, so each lane runs
+    // only the arithmetic of the event it met.
     if (hit) {
       // Face: smooth-dielectric Fresnel, reflect with probability F.
+      p.z = zface;
       reflect = !cross && fresnel_reflects(fabsf(p.uz), c.n_rel, u1);
       if (reflect) p.uz = -p.uz;
     } else {
+      p.z = __fmaf_rn(dist, p.uz, p.z);
       // Collision: albedo weighting with roulette, or analog absorption.
       if (c.mode == 0) {
         // the surviving weight W alpha and the deposit W - W alpha (one rounding)
@@ -525,51 +526,56 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
       scatter_direction(p, mu, u2);
     }
   } else {
-    // Hero-wavelength members (HERO = C > 1): every lane evaluates both the
-    // face and the collision arithmetic and selects, since the members'
-    // density ratios take terms from both.
-    reflect = hit && !cross && fresnel_reflects(fabsf(p.uz), c.n_rel, u1);
-    // collision: the members' flight density exp(-sigma dist), and on a
-    // collision sigma and the albedo.  Roulette is decided on the largest
-    // member weight Wr and boosts every member by rr_th / Wr.
-    const float Wn = __fmul_rn(p.W, p.alpha);
-    const float An = __fadd_rn(__fmaf_rn(p.W, -p.alpha, p.W), p.Aacc);
-    const float coll = hit ? 0.0f : 1.0f;
-    float Wm[HERO > 1 ? HERO - 1 : 1];
-    float Wr = Wn;
+    // Hero-wavelength members (HERO = C > 1), the same two branches.  Every
+    // draw adds each member's flight density term (sigma_h - sigma_m) dist
+    // log2 e; a collision adds the members' log2(sigma_m / sigma_h), weights
+    // and Henyey-Greenstein density ratios.
 #pragma unroll
-    for (int m = 0; m < HERO - 1; ++m) {
-      hs.D[m] = __fmaf_rn(coll, hs.ls[m], __fmaf_rn(hs.ds[m], dist, hs.D[m]));
-      Wm[m] = __fmul_rn(hs.W[m], hs.a[m]);
-      Wr = fmaxf(Wr, Wm[m]);
+    for (int m = 0; m < HERO - 1; ++m) hs.D[m] = __fmaf_rn(hs.ds[m], dist, hs.D[m]);
+    if (hit) {
+      p.z = zface;
+      reflect = !cross && fresnel_reflects(fabsf(p.uz), c.n_rel, u1);
+      if (reflect) p.uz = -p.uz;
+    } else {
+      p.z = __fmaf_rn(dist, p.uz, p.z);
+      // Roulette is decided on the largest member weight Wr and boosts every
+      // member by rr_th / Wr.
+      const float Wn = __fmul_rn(p.W, p.alpha);
+      const float An = __fadd_rn(__fmaf_rn(p.W, -p.alpha, p.W), p.Aacc);
+      float Wm[HERO > 1 ? HERO - 1 : 1];
+      float Wr = Wn;
+#pragma unroll
+      for (int m = 0; m < HERO - 1; ++m) {
+        hs.D[m] = __fadd_rn(hs.ls[m], hs.D[m]);
+        Wm[m] = __fmul_rn(hs.W[m], hs.a[m]);
+        Wr = fmaxf(Wr, Wm[m]);
+      }
+      const bool low = Wr < c.rr_th;
+      dead = low && !(u3 < __fmul_rn(Wr, c.inv_rr_th));
+      const float boost = __fmul_rn(c.rr_th, rcp_approx(Wr));
+      p.W = low ? (Wn == Wr ? c.rr_th : __fmul_rn(Wn, boost)) : Wn;
+#pragma unroll
+      for (int m = 0; m < HERO - 1; ++m)
+        hs.W[m] = low ? (Wm[m] == Wr ? c.rr_th : __fmul_rn(Wm[m], boost)) : Wm[m];
+      p.Aacc = An;
+      p.n_coll += 1u;
+      // Henyey-Greenstein scattering with the hero's g, and the members'
+      //   log2 p_HG(mu; g_m) - log2 p_HG(mu; g_h)
+      //   = log2((1-g_m^2)/(1-g_h^2)) - 1.5 (log2(1+g_m^2-2 g_m mu) - log2(1+g_h^2-2 g_h mu))
+      const float mu = hg_mu(p.g, p.hc1, p.hc2, u1);
+      if (!dead) {
+        const float lh =
+            lg2_approx(__fmaf_rn(__fmul_rn(-2.0f, p.g), mu, __fmaf_rn(p.g, p.g, 1.0f)));
+#pragma unroll
+        for (int m = 0; m < HERO - 1; ++m) {
+          const float gm = hs.g[m];
+          const float lm =
+              lg2_approx(__fmaf_rn(__fmul_rn(-2.0f, gm), mu, __fmaf_rn(gm, gm, 1.0f)));
+          hs.D[m] = __fadd_rn(__fmaf_rn(-1.5f, __fsub_rn(lm, lh), hs.cg[m]), hs.D[m]);
+        }
+      }
+      scatter_direction(p, mu, u2);
     }
-    const bool low = Wr < c.rr_th;
-    dead = !hit && low && !(u3 < __fmul_rn(Wr, c.inv_rr_th));
-    const float boost = __fmul_rn(c.rr_th, rcp_approx(Wr));
-    p.W = hit ? p.W : (low ? (Wn == Wr ? c.rr_th : __fmul_rn(Wn, boost)) : Wn);
-#pragma unroll
-    for (int m = 0; m < HERO - 1; ++m)
-      hs.W[m] = hit ? hs.W[m]
-                    : (low ? (Wm[m] == Wr ? c.rr_th : __fmul_rn(Wm[m], boost)) : Wm[m]);
-    p.Aacc = hit ? p.Aacc : An;
-    p.n_coll += hit ? 0u : 1u;
-    // Henyey-Greenstein scattering with the hero's g, and the members'
-    //   log2 p_HG(mu; g_m) - log2 p_HG(mu; g_h)
-    //   = log2((1-g_m^2)/(1-g_h^2)) - 1.5 (log2(1+g_m^2-2 g_m mu) - log2(1+g_h^2-2 g_h mu))
-    const float mu = hg_mu(p.g, p.hc1, p.hc2, u1);
-    const float scat = (hit || dead) ? 0.0f : 1.0f;
-    const float lh = lg2_approx(__fmaf_rn(__fmul_rn(-2.0f, p.g), mu, __fmaf_rn(p.g, p.g, 1.0f)));
-#pragma unroll
-    for (int m = 0; m < HERO - 1; ++m) {
-      const float gm = hs.g[m];
-      const float lm = lg2_approx(__fmaf_rn(__fmul_rn(-2.0f, gm), mu, __fmaf_rn(gm, gm, 1.0f)));
-      hs.D[m] = __fmaf_rn(scat, __fmaf_rn(-1.5f, __fsub_rn(lm, lh), hs.cg[m]), hs.D[m]);
-    }
-    const float ux0 = p.ux, uy0 = p.uy, uz0 = p.uz;
-    scatter_direction(p, mu, u2);
-    p.ux = hit ? ux0 : p.ux;
-    p.uy = hit ? uy0 : p.uy;
-    p.uz = hit ? (reflect ? -uz0 : uz0) : p.uz;
   }
 
   if (LAYERED && cross) {  // continue in the other layer with a fresh flight
