@@ -58,8 +58,8 @@ DECODER_MACS_PER_TEXEL = (3 * 256 + 256 * 256 + 256 * 5) + (5 * 512 + 512 * 512 
 # dram__bytes_write.sum) of the 1024-texel case, scaled by 64 to the
 # 65536-texel launch (the traffic grows with the instances walked).  Valid
 # only while the kernel sources are the ones captured (sha1 below).
-WALK_TRAFFIC = {"bytes_per_launch": (61.662976e6 + 11.868416e6) * 64,
-                "source_sha1": "aaa79bd8e02a7bca1ab7e1d17990202931176723"}
+WALK_TRAFFIC = {"bytes_per_launch": (61.675776e6 + 11.411456e6) * 64,
+                "source_sha1": "77c502db92a6c217e5160f3766a85c892f43ae63"}
 
 
 def _walk_source_sha1():
