@@ -77,6 +77,36 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Tiled TMA store of one box from shared memory (bulk-group completion).
+// Elements of the box outside the tensor are not written.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(src), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the thread's committed bulk stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// the thread's committed bulk stores have completed
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+// orders this thread's shared-memory writes before later async-proxy reads
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -154,8 +184,11 @@ __device__ __forceinline__ float sigmoid_fast(float x) {
   return __fmaf_rn(0.5f, tanh_fast(0.5f * x), 0.5f);
 }
 
+// One tanh.approx per element for either activation: sigmoid(x) is taken
+// as (1 + tanh(x / 2)) / 2, the same operations as sigmoid_fast.
 __device__ __forceinline__ float activate(float x, int act) {
-  return act == ACT_TANH ? tanh_fast(x) : act == ACT_SIGMOID ? sigmoid_fast(x) : x;
+  const float t = tanh_fast(act == ACT_SIGMOID ? 0.5f * x : x);
+  return act == ACT_TANH ? t : act == ACT_SIGMOID ? __fmaf_rn(0.5f, t, 0.5f) : x;
 }
 
 template <int COLS>
@@ -190,6 +223,41 @@ __device__ __forceinline__ void epi_hidden_chunk(const float* v, int row, int co
 #pragma unroll
     for (int j = 0; j < 16; ++j)
       if (col + j < ep.n_valid) d16[j] = (uint16_t)(w[j >> 1] >> ((j & 1) * 16));
+  }
+}
+
+// Hidden layer, TMA-store form: one 64-column block of a warp's 32 rows.
+// The BF16 results go to the warp's 4 KB staging buffer in the 128-byte
+// swizzled layout of the output tensor map (row r at r * 128 bytes, 16-byte
+// chunk c at position c ^ (r & 7), so the eight rows of each store phase hit
+// distinct banks), and one lane issues the tensor store.  The previous block's
+// store must have finished reading the buffer before it is overwritten.
+__device__ __forceinline__ void epi_hidden_block_tma(const float* v, const float* __restrict__ bias,
+                                                     int col, int act, uint32_t stg, int lane,
+                                                     const CUtensorMap* tmap_c, int y) {
+  uint32_t w[32];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float4 b0 = __ldg(reinterpret_cast<const float4*>(bias + col + c * 8));
+    const float4 b1 = __ldg(reinterpret_cast<const float4*>(bias + col + c * 8 + 4));
+    const float* x = v + c * 8;
+    w[4 * c + 0] = pack_bf16x2(activate(x[0] + b0.x, act), activate(x[1] + b0.y, act));
+    w[4 * c + 1] = pack_bf16x2(activate(x[2] + b0.z, act), activate(x[3] + b0.w, act));
+    w[4 * c + 2] = pack_bf16x2(activate(x[4] + b1.x, act), activate(x[5] + b1.y, act));
+    w[4 * c + 3] = pack_bf16x2(activate(x[6] + b1.z, act), activate(x[7] + b1.w, act));
+  }
+  if (lane == 0) bulk_wait_read_all();
+  __syncwarp();
+  const uint32_t row = stg + (uint32_t)lane * 128u;
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    st_shared_v4(row + ((uint32_t)(c ^ (lane & 7)) << 4), w[4 * c], w[4 * c + 1], w[4 * c + 2],
+                 w[4 * c + 3]);
+  fence_proxy_async_smem();
+  __syncwarp();
+  if (lane == 0) {
+    tma_store_2d(tmap_c, stg, col, y);
+    bulk_commit();
   }
 }
 
@@ -252,35 +320,51 @@ __device__ __forceinline__ void epi_final_group(const float* v, int row, int P,
 // through the shared-memory ring without stopping between tiles; warp 1
 // issues the MMAs into one of two TMEM accumulators; warps 2..9 drain the
 // other accumulator (two warps per TMEM lane quarter, alternate 16-column
-// chunks), so a tile's epilogue overlaps the next tile's MMAs.  The bias
-// vector is staged once in shared memory.  Every CTA loads its own A and B
-// tiles with its own TMA copies into its own shared memory.
+// chunks), so a tile's epilogue overlaps the next tile's MMAs.  Hidden
+// layers with N tiles of 64 columns or more write their BF16 output with TMA
+// tensor stores from a 4 KB staging buffer per epilogue warp (whole 64-column
+// blocks per warp) and read the bias through the read-only cache; the other
+// layers stage the bias in shared memory and store from registers.  Every CTA
+// loads its own A and B tiles with its own TMA copies into its own shared
+// memory.
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kStagingBytes = 4096;  // per epilogue warp: 32 rows x 64 BF16 columns
+
+template <int BN, int EPI>
+struct GemmSmem {
+  static constexpr bool kTmaStore = EPI == EPI_HIDDEN && BN >= 64;
+  static constexpr int kStaging = kTmaStore ? kEpiWarps * kStagingBytes : 0;
+};
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
-                 const __grid_constant__ CUtensorMap tmap_b, int a_x0, int num_kb,
+                 const __grid_constant__ CUtensorMap tmap_b,
+                 const __grid_constant__ CUtensorMap tmap_c, int a_x0, int num_kb,
                  int n_tiles, long long m_tiles, const float* __restrict__ bias, EpiParams ep,
                  unsigned int* status) {
   constexpr int A_BYTES = BM * BK * 2;
   constexpr int B_BYTES = BN * BK * 2;
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   constexpr int TCOLS = TmemCols<2 * BN>::value2;
+  constexpr int ACC_STRIDE = TCOLS / 2;  // TMEM columns between the two accumulators
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
   static_assert(B_BYTES % 1024 == 0, "tiles must stay 1024-byte aligned");
+  constexpr bool kTmaStore = GemmSmem<BN, EPI>::kTmaStore;
+  constexpr int STAGING = GemmSmem<BN, EPI>::kStaging;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint8_t* staging = smem + STAGES * STAGE_BYTES;  // kTmaStore: 1024-byte aligned
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + STAGING);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;   // accumulator b ready for the epilogue
   uint64_t* tempty = tfull + 2;       // accumulator b drained by the epilogue
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   volatile uint32_t* abort_flag = tmem_slot + 1;
-  float* sbias = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
+  float* sbias = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + STAGING + 256);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -308,7 +392,8 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  for (int j = threadIdx.x; j < n_tiles * BN; j += blockDim.x) sbias[j] = bias[j];
+  if constexpr (!kTmaStore)
+    for (int j = threadIdx.x; j < n_tiles * BN; j += blockDim.x) sbias[j] = bias[j];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -320,6 +405,9 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                    : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap_b))
                    : "memory");
+      if constexpr (kTmaStore)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap_c))
+                     : "memory");
       long long it = 0;
       for (long long t = first; t < total && !*abort_flag; t += step) {
         const int m_tile = (int)(t / n_tiles), n_tile = (int)(t % n_tiles);
@@ -351,7 +439,7 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
           break;
         }
         tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        const uint32_t acc = tmem + (uint32_t)(b * ACC_STRIDE);
         for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = (int)(it % STAGES);
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -388,8 +476,39 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
       }
       tc_fence_after();
       const int row = m_tile * BM + q * 32 + lane;
-      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
-      if (EPI == EPI_HIDDEN) {
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * ACC_STRIDE);
+      if constexpr (kTmaStore) {
+        // read this warp's 64-column blocks of the accumulator rows, release
+        // TMEM, then activate and store block by block
+        constexpr int NBLK = BN / 64;
+        constexpr int MYB = (NBLK + 1) / 2;
+        float v[MYB * 64];
+#pragma unroll
+        for (int j = 0; j < MYB; ++j) {
+          const int blk = 2 * j + half;
+          if (blk < NBLK) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tmem_ld16(taddr + blk * 64 + c * 16, v + j * 64 + c * 16);
+          }
+        }
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                        smem_u32(&tempty[b]))
+                                    : "memory");
+        const int y = m_tile * BM + q * 32;
+        if (y < ep.M) {  // (a box wholly below the last row writes nothing)
+#pragma unroll
+          for (int j = 0; j < MYB; ++j) {
+            const int blk = 2 * j + half;
+            if (blk < NBLK)
+              epi_hidden_block_tma(v + j * 64, bias, n_tile * BN + blk * 64, ep.act,
+                                   smem_u32(staging + (warp - 2) * kStagingBytes), lane,
+                                   &tmap_c, y);
+          }
+        }
+      } else if (EPI == EPI_HIDDEN) {
         // read this warp's chunks of the accumulator row, release TMEM, then
         // finish the math and the stores
         constexpr int NCH = BN / 16;
@@ -427,6 +546,9 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                                     : "memory");
       }
     }
+    // the staging buffers stay allocated until the warp's stores are done
+    if constexpr (kTmaStore)
+      if (lane == 0) bulk_wait_all();
   }
   tc_fence_before();
   __syncthreads();
@@ -443,13 +565,19 @@ gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
 __global__ void __launch_bounds__(256)
 enc0_kernel(const float* __restrict__ rgb, long long T, const __nv_bfloat16* __restrict__ W,
             const float* __restrict__ b, __nv_bfloat16* __restrict__ out) {
-  __shared__ float sw[256 * 3 + 256];
-  for (int i = threadIdx.x; i < 256 * 4; i += blockDim.x)
-    sw[i] = i < 768 ? __bfloat162float(W[i]) : b[i - 768];
-  __syncthreads();
-  // one warp per texel row, each lane 8 outputs (16-byte store); a grid of a
-  // few blocks per SM strides over the rows so the weights load once per block
+  // one warp per texel row, each lane 8 outputs (16-byte store); a lane
+  // computes the same 8 outputs for every row, so its 32 weights and biases
+  // stay in registers; a grid of a few blocks per SM strides over the rows
   const int lane = threadIdx.x & 31;
+  float w0[8], w1[8], w2[8], bb[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int o = lane * 8 + e;
+    w0[e] = __bfloat162float(W[o * 3 + 0]);
+    w1[e] = __bfloat162float(W[o * 3 + 1]);
+    w2[e] = __bfloat162float(W[o * 3 + 2]);
+    bb[e] = b[o];
+  }
   const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long rowg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; rowg < T;
        rowg += warps) {
@@ -460,10 +588,8 @@ enc0_kernel(const float* __restrict__ rgb, long long T, const __nv_bfloat16* __r
       float z2[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        const int o = lane * 8 + 2 * j + e;
-        z2[e] = tanh_fast(__fmaf_rn(sw[o * 3 + 0], r,
-                                    __fmaf_rn(sw[o * 3 + 1], g,
-                                              __fmaf_rn(sw[o * 3 + 2], bl, sw[768 + o]))));
+        const int i = 2 * j + e;
+        z2[e] = tanh_fast(__fmaf_rn(w0[i], r, __fmaf_rn(w1[i], g, __fmaf_rn(w2[i], bl, bb[i]))));
       }
       h[j] = pack_bf16x2(z2[0], z2[1]);
     }
@@ -512,14 +638,17 @@ cudaError_t launch_bounded_wait_selftest(unsigned int* status, long long limit, 
 
 // ---------------------------------------------------------------- launch --
 template <int BN, int EPI>
-static cudaError_t launch_gemm_t(const CUtensorMap& ta, const CUtensorMap& tb, int a_x0,
-                                 int num_kb, int n_tiles, long long m_tiles, const float* bias,
-                                 const EpiParams& ep, unsigned int* status, cudaStream_t st) {
+static cudaError_t launch_gemm_t(const CUtensorMap& ta, const CUtensorMap& tb,
+                                 const CUtensorMap& tc, int a_x0, int num_kb, int n_tiles,
+                                 long long m_tiles, const float* bias, const EpiParams& ep,
+                                 unsigned int* status, cudaStream_t st) {
   // at least half of the SM's shared memory, so exactly one CTA (and one
-  // TMEM allocation of up to 512 columns) per SM
+  // TMEM allocation of up to 512 columns) per SM; the largest case (N = 256,
+  // TMA stores) is 192 + 32 + 1.25 KB of the 227 KB a block may have
   constexpr size_t ring = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2);
-  const size_t smem = (ring > 120 * 1024 ? ring : 120 * 1024) + 1024 + 256 +
-                      (size_t)n_tiles * BN * sizeof(float);
+  constexpr size_t staging = (size_t)GemmSmem<BN, EPI>::kStaging;
+  const size_t smem = (ring > 120 * 1024 ? ring : 120 * 1024) + staging + 1024 + 256 +
+                      (GemmSmem<BN, EPI>::kTmaStore ? 0 : (size_t)n_tiles * BN * sizeof(float));
   auto fn = gemm_bf16_kernel<BN, EPI>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -530,21 +659,22 @@ static cudaError_t launch_gemm_t(const CUtensorMap& ta, const CUtensorMap& tb, i
   if (total == 0) return cudaSuccess;
   // persistent: one CTA per SM (its shared memory allows no second one)
   const long long ctas = total < sms ? total : sms;
-  fn<<<(unsigned)ctas, kThreads, smem, st>>>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep,
-                                             status);
+  fn<<<(unsigned)ctas, kThreads, smem, st>>>(ta, tb, tc, a_x0, num_kb, n_tiles, m_tiles, bias,
+                                             ep, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemm(int bn, int epi, const CUtensorMap& ta, const CUtensorMap& tb,
-                        int a_x0, int num_kb, int n_tiles, long long m_tiles, const float* bias,
-                        const EpiParams& ep, unsigned int* status, cudaStream_t st) {
+                        const CUtensorMap& tc, int a_x0, int num_kb, int n_tiles,
+                        long long m_tiles, const float* bias, const EpiParams& ep,
+                        unsigned int* status, cudaStream_t st) {
 #define SSS_GEMM(BN_, EPI_) \
-  return launch_gemm_t<BN_, EPI_>(ta, tb, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st)
+  return launch_gemm_t<BN_, EPI_>(ta, tb, tc, a_x0, num_kb, n_tiles, m_tiles, bias, ep, status, st)
   if (epi == EPI_FINAL && bn == kFinalBN) SSS_GEMM(kFinalBN, EPI_FINAL);
   if (epi == EPI_HIDDEN) {
     switch (bn) {
       case 16: SSS_GEMM(16, EPI_HIDDEN);
-      case 128: SSS_GEMM(128, EPI_HIDDEN);
+      case 192: SSS_GEMM(192, EPI_HIDDEN);
       case 256: SSS_GEMM(256, EPI_HIDDEN);
     }
   }

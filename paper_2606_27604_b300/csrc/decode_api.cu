@@ -97,13 +97,15 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D bf16 tensor map over [rows][cols] (row pitch = cols), box 64 x box_rows,
-// 128-byte swizzle; reads outside the tensor return zeros.
-bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+// 2-D bf16 tensor map over [rows][cols] with a row pitch of `pitch` elements
+// (0: cols), box 64 x box_rows, 128-byte swizzle; loads outside the tensor
+// return zeros and stores outside it write nothing.
+bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows,
+              uint64_t pitch = 0) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {cols * 2};
+  cuuint64_t strides[1] = {(pitch ? pitch : cols) * 2};
   cuuint32_t box[2] = {64, box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
@@ -220,7 +222,7 @@ static sss_status decode_impl(const float* rgb, int64_t T, const void* packed, v
       {X1, 256, 0, 2, 16, EPI_HIDDEN, buf[BUF_T], 384, 376, 5, ACT_SIGMOID},
       {buf[BUF_T], 384, 376, 3, 256, EPI_HIDDEN, buf[BUF_R1], 512, 0, 512, ACT_TANH},
       {buf[BUF_R1], 512, 0, 4, 256, EPI_HIDDEN, buf[BUF_R2], 512, 0, 512, ACT_TANH},
-      {buf[BUF_R2], 512, 0, 5, 128, EPI_HIDDEN, buf[BUF_T], 384, 0, 376, ACT_SIGMOID},
+      {buf[BUF_R2], 512, 0, 5, 192, EPI_HIDDEN, buf[BUF_T], 384, 0, 376, ACT_SIGMOID},
       {buf[BUF_T], 384, 0, 6, 256, EPI_HIDDEN, buf[BUF_A], 768, 0, 768, ACT_TANH},
       {buf[BUF_A], 768, 0, 7, 256, EPI_HIDDEN, buf[BUF_B], 768, 0, 768, ACT_TANH},
       {buf[BUF_B], 768, 0, 8, 256, EPI_HIDDEN, buf[BUF_A], 768, 0, 768, ACT_TANH},
@@ -228,10 +230,20 @@ static sss_status decode_impl(const float* rgb, int64_t T, const void* packed, v
   };
   for (const Step& s : steps) {
     const LayerSpec& L = kLayers[s.layer];
-    CUtensorMap ta, tb;
+    CUtensorMap ta, tb, tc;
     if (!make_map(&ta, s.a, (uint64_t)T, (uint64_t)s.a_cols, 128) ||
         !make_map(&tb, W(s.layer), (uint64_t)L.rows, (uint64_t)L.cols, (uint32_t)s.bn))
       return SSS_ERR_CUDA;
+    // hidden layers with 64-column blocks store through an output map whose
+    // width is the valid columns, so a ragged last block is clipped
+    const bool tma_store = s.epi == EPI_HIDDEN && s.bn >= 64;
+    if (tma_store) {
+      if (s.col0 != 0 || !make_map(&tc, s.out, (uint64_t)T, (uint64_t)s.n_valid, 32,
+                                   (uint64_t)s.ldc))
+        return SSS_ERR_CUDA;
+    } else {
+      tc = tb;  // not read
+    }
     EpiParams ep{};
     ep.out = s.out;
     ep.ldc = s.ldc;
@@ -248,8 +260,8 @@ static sss_status decode_impl(const float* rgb, int64_t T, const void* packed, v
     ep.M = T;
     const int num_kb = (L.cols + 63) / 64;
     const int n_tiles = L.rows / s.bn;
-    if (launch_gemm(s.bn, s.epi, ta, tb, s.a_x0, num_kb, n_tiles, mt, B(s.layer), ep, status,
-                    st) != cudaSuccess)
+    if (launch_gemm(s.bn, s.epi, ta, tb, tc, s.a_x0, num_kb, n_tiles, mt, B(s.layer), ep,
+                    status, st) != cudaSuccess)
       return SSS_ERR_CUDA;
   }
   return SSS_OK;

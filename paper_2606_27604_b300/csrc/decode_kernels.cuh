@@ -52,9 +52,12 @@ struct EpiParams {
 
 cudaError_t launch_bounded_wait_selftest(unsigned int* status, long long limit,
                                          cudaStream_t st);
+// tc: the output tensor map of hidden layers with bn >= 64 (box 64 x 32,
+// 128-byte swizzle), written by TMA stores; unused otherwise.
 cudaError_t launch_gemm(int bn, int epi, const CUtensorMap& ta, const CUtensorMap& tb,
-                        int a_x0, int num_kb, int n_tiles, long long m_tiles, const float* bias,
-                        const EpiParams& ep, unsigned int* status, cudaStream_t st);
+                        const CUtensorMap& tc, int a_x0, int num_kb, int n_tiles,
+                        long long m_tiles, const float* bias, const EpiParams& ep,
+                        unsigned int* status, cudaStream_t st);
 cudaError_t launch_enc0(const float* rgb, long long T, const __nv_bfloat16* W, const float* b,
                         __nv_bfloat16* out, cudaStream_t st);
 cudaError_t launch_pack(const __nv_bfloat16* src, int src_rows, int src_cols, __nv_bfloat16* dst,
