@@ -376,6 +376,8 @@ def main():
     ap.add_argument("--no-baselines", action="store_true",
                     help="skip the uneven-batch and plain one-launch-per-instance timings")
     ap.add_argument("--no-decoder", action="store_true")
+    ap.add_argument("--decoder-side", type=int, default=1024,
+                    help="texture side of the decoder line (default 1024; smaller for profiling)")
     ap.add_argument("--no-hero", action="store_true",
                     help="skip the hero-wavelength comparison")
     ap.add_argument("--no-probe", action="store_true",
@@ -672,7 +674,7 @@ def main():
     decoder = None
     if not args.no_decoder and ws == 1:
         from paper_2606_27604_b300 import inputs
-        side = 1024
+        side = args.decoder_side
         rgb = torch.from_numpy(inputs.rgb_texture(side=side, seed=4)).to(dev)
         packed = api.decoder_pack(inputs.decoder_weights(seed=4), device=dev)
         dws = torch.empty(api.lib.sss_decode_workspace_size(side * side), dtype=torch.uint8,
