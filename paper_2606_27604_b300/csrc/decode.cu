@@ -319,12 +319,14 @@ __device__ __forceinline__ void epi_final_group(const float* v, int row, int P,
 // working at one time share rows of A in L2).  Warp 0 streams A/B k-blocks
 // through the shared-memory ring without stopping between tiles; warp 1
 // issues the MMAs into one of two TMEM accumulators; warps 2..9 drain the
-// other accumulator (two warps per TMEM lane quarter, alternate 16-column
-// chunks), so a tile's epilogue overlaps the next tile's MMAs.  Hidden
-// layers with N tiles of 64 columns or more write their BF16 output with TMA
-// tensor stores from a 4 KB staging buffer per epilogue warp (whole 64-column
-// blocks per warp) and read the bias through the read-only cache; the other
-// layers stage the bias in shared memory and store from registers.  Every CTA
+// other accumulator (two warps per TMEM lane quarter), so a tile's epilogue
+// overlaps the next tile's MMAs.  Hidden layers with N tiles of 64 columns
+// or more split the quarter's columns into whole 64-column blocks, alternating
+// between its two warps, write their BF16 output with TMA tensor stores from
+// a 4 KB staging buffer per epilogue warp and read the bias through the
+// read-only cache; the 16-column layer (alternate 16-column chunks) and the
+// last layer (alternate column groups) stage the bias in shared memory and
+// store from registers.  Every CTA
 // loads its own A and B tiles with its own TMA copies into its own shared
 // memory.
 constexpr int kEpiWarps = 8;
