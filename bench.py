@@ -145,8 +145,9 @@ def spectral_inputs(rank):
                                  n_paths=WORKLOAD["paths_per_instance"], n_rel=1.4)
 
 
-def cpu_baseline_sample(n_texels=24):
-    """The FP64 oracle on a bounded sample of the workload (host cores)."""
+def cpu_baseline_sample(n_texels=64, with_other_configs=True):
+    """The FP64 oracle on a bounded sample of the workload (host cores); with
+    `with_other_configs`, also on bounded samples of the other workloads."""
     import oracle
     from paper_2606_27604_b300 import inputs
     x = inputs.spectral_field(n_texels=n_texels, param_seed=WORKLOAD["param_seed"],
@@ -156,7 +157,18 @@ def cpu_baseline_sample(n_texels=24):
     oracle.walk(x.alpha, x.sigma_t, x.g, x.w, x.n_paths, None, x.n_rel, o)
     dt = time.perf_counter() - t0
     paths = int(x.n_paths.sum())
-    # the other configurations' shapes, each a bounded sample
+    res = {"value": paths / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{n_texels} texels x 81 bands x 4096 paths ({paths} paths) of the "
+                     f"spectral workload, FP64, {dt:.1f} s"}
+    if with_other_configs:
+        res["other_configs"] = cpu_other_configs()
+    return res
+
+
+def cpu_other_configs():
+    """The FP64 oracle on bounded samples of the other workloads' shapes."""
+    import oracle
+    from paper_2606_27604_b300 import inputs
     per_config = {}
     x0 = inputs.single_wavelength(param_seed=0, n_paths=1 << 18)
     o0 = oracle.OracleOpts(nbins=32, r_max_mm=10.0, seed=1000)
@@ -178,10 +190,7 @@ def cpu_baseline_sample(n_texels=24):
         "sample": f"every 64th of the 4096 uneven instances ({xu.n_inst} instances, {pu} paths), "
                   f"{du:.1f} s",
         "steps_per_path": float(np.average(ru["steps"], weights=xu.n_paths))}
-    return {"value": paths / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n_texels} texels x 81 bands x 4096 paths ({paths} paths) of the "
-                      f"spectral workload, FP64, {dt:.1f} s",
-            "other_configs": per_config}
+    return per_config
 
 
 def pipeline_leg(side=1024, oracle_block=32, dev_index=0):
@@ -345,11 +354,12 @@ def run_reference(args):
         return 0
     per_step = []
     for _ in range(args.warmup):
-        cpu_baseline_sample(args.ref_texels)
+        cpu_baseline_sample(args.ref_texels, with_other_configs=False)
     res = None
     for _ in range(args.steps):
-        res = cpu_baseline_sample(args.ref_texels)
+        res = cpu_baseline_sample(args.ref_texels, with_other_configs=False)
         per_step.append(res["value"])
+    res["other_configs"] = cpu_other_configs()
     v = float(np.mean(per_step))
     paths_per_step = args.ref_texels * 81 * 4096
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
