@@ -58,8 +58,8 @@ DECODER_MACS_PER_TEXEL = (3 * 256 + 256 * 256 + 256 * 5) + (5 * 512 + 512 * 512 
 # dram__bytes_write.sum) of the 1024-texel case, scaled by 64 to the
 # 65536-texel launch (the traffic grows with the instances walked).  Valid
 # only while the kernel sources are the ones captured (sha1 below).
-WALK_TRAFFIC = {"bytes_per_launch": (61.675776e6 + 11.411456e6) * 64,
-                "source_sha1": "77c502db92a6c217e5160f3766a85c892f43ae63"}
+WALK_TRAFFIC = {"bytes_per_launch": (61.70496e6 + 11.221504e6) * 64,
+                "source_sha1": "99fb3fb6d1fbd7e0e34e140e7182d0b8185e9a87"}
 
 
 def _walk_source_sha1():
@@ -736,7 +736,8 @@ def main():
         WORKLOAD["texels"] == 256 * 256 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "walk_persistent_kernel<false, false, 0, true> (semi-infinite slabs)",
+                "kernel": "walk_persistent_kernel<false, false, 0, true, 0> (semi-infinite slabs, "
+                          "albedo weighting)",
                 "peak_basis": f"{sms} SMs x {SM_LANES_PER_CLK} FP32/INT32 lanes/clk x "
                               f"{f_mhz:.0f} MHz (median SM clock sampled in the timed region)",
                 "ops_per_step": ALG_ALU_OPS_PER_STEP, "steps_per_launch": total_draws,

@@ -254,7 +254,7 @@ sss_status persistent_shape(bool adj, const sss_params* p, const sss_walk_opts* 
   if (sh->block / 32 > max_warps) sh->block = max_warps * 32;
   sh->smem = (size_t)(sh->block / 32) * per_warp;
   const void* fn = persistent_kernel_ptr(adj, p->alpha2 != nullptr, o->hero_bands,
-                                         p->thickness_mm == nullptr);
+                                         p->thickness_mm == nullptr, o->mode);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit) !=
       cudaSuccess)
     return SSS_ERR_CUDA;

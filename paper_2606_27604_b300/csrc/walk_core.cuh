@@ -447,7 +447,9 @@ __device__ __forceinline__ void scatter_direction(Path& p, float mu, float u) {
 // runs each with the lanes that met that event.  SEMI = true compiles the
 // semi-infinite slab (no far face: p.d is +inf), where only the entry face
 // can be met; the results are those of the general form for d = +inf.
-template <bool ADJ, bool LAYERED = false, int HERO = 0, bool SEMI = false>
+// MODE fixes the collision rule at compile time (0 albedo weighting with
+// roulette, 1 analog absorption) or, at -1, takes it from c.mode.
+template <bool ADJ, bool LAYERED = false, int HERO = 0, bool SEMI = false, int MODE = -1>
 __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<HERO>& hs) {
   if (p.step >= c.max_steps) return EV_TRUNC;
   const uint4 r = philox_step(p.step, p.pc, c.rk);
@@ -502,7 +504,7 @@ __device__ __forceinline__ int path_step(const WalkConst& c, Path& p, HeroState<
     } else {
       p.z = __fmaf_rn(dist, p.uz, p.z);
       // Collision: albedo weighting with roulette, or analog absorption.
-      if (c.mode == 0) {
+      if (MODE < 0 ? c.mode == 0 : MODE == 0) {
         // the surviving weight W alpha and the deposit W - W alpha (one rounding)
         const float Wn = __fmul_rn(p.W, p.alpha);
         const float An = __fadd_rn(__fmaf_rn(p.W, -p.alpha, p.W), p.Aacc);

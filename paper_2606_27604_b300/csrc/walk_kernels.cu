@@ -490,7 +490,7 @@ __device__ __forceinline__ void tally_exit_warp(const WalkConst& c, const WalkSc
 // scheduled "instance" is a hero group of C bands, and a slot holds the C
 // members' accumulators.
 // SEMI: every instance is a semi-infinite slab (no thickness array).
-template <bool ADJ, bool LAYERED, int HERO, bool SEMI>
+template <bool ADJ, bool LAYERED, int HERO, bool SEMI, int MODE>
 __global__ void __launch_bounds__(256, (HERO >= 4 || (ADJ && LAYERED))
                                            ? 3 : ((ADJ || LAYERED || HERO) ? 4 : 5))
 walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
@@ -678,7 +678,7 @@ walk_persistent_kernel(WalkConst c, WalkSched s, TallyOut t, GradIn gi) {
     }
     // ---- advance every running path by one draw ----
     if (st == LANE_RUNNING) {
-      const int ev = path_step<ADJ, LAYERED, HERO, SEMI>(c, p, hs);
+      const int ev = path_step<ADJ, LAYERED, HERO, SEMI, MODE>(c, p, hs);
       if (ev != EV_CONTINUE) st = LANE_RUNNING + ev;
     }
   }
@@ -849,21 +849,26 @@ void launch_walk_persistent(bool adj, int grid, int block, size_t smem, const Wa
                             const WalkSched& s, const TallyOut& t, const GradIn& gi,
                             cudaStream_t st) {
   const void* fn = persistent_kernel_ptr(adj, c.alpha2 != nullptr, c.hero,
-                                         c.thickness == nullptr);
+                                         c.thickness == nullptr, c.mode);
   void* args[] = {const_cast<WalkConst*>(&c), const_cast<WalkSched*>(&s),
                   const_cast<TallyOut*>(&t), const_cast<GradIn*>(&gi)};
   cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
 // Semi-infinite batches (no thickness array) take the SEMI instantiations;
-// two-layer slabs keep the general one.
-const void* persistent_kernel_ptr(bool adj, bool layered, int hero, bool semi) {
-#define SSS_K(A, L, H) (semi ? (const void*)walk_persistent_kernel<A, L, H, true> \
-                             : (const void*)walk_persistent_kernel<A, L, H, false>)
+// two-layer slabs keep the general one.  Single-layer walks in the default
+// weighting mode take instantiations with the collision rule fixed at
+// compile time (no uniform branch per collision); the rest read c.mode.
+const void* persistent_kernel_ptr(bool adj, bool layered, int hero, bool semi, int mode) {
+#define SSS_K(A, L, H) (semi ? (const void*)walk_persistent_kernel<A, L, H, true, -1> \
+                             : (const void*)walk_persistent_kernel<A, L, H, false, -1>)
+#define SSS_KW(A) (semi ? (const void*)walk_persistent_kernel<A, false, 0, true, 0> \
+                        : (const void*)walk_persistent_kernel<A, false, 0, false, 0>)
+  if (!layered && hero == 0 && mode == 0) return adj ? SSS_KW(true) : SSS_KW(false);
   if (adj)
-    return layered ? (const void*)walk_persistent_kernel<true, true, 0, false>
+    return layered ? (const void*)walk_persistent_kernel<true, true, 0, false, -1>
                    : SSS_K(true, false, 0);
-  if (layered) return (const void*)walk_persistent_kernel<false, true, 0, false>;
+  if (layered) return (const void*)walk_persistent_kernel<false, true, 0, false, -1>;
   switch (hero) {
     case 1: return SSS_K(false, false, 1);
     case 2: return SSS_K(false, false, 2);
@@ -872,6 +877,7 @@ const void* persistent_kernel_ptr(bool adj, bool layered, int hero, bool semi) {
     default: return SSS_K(false, false, 0);
   }
 #undef SSS_K
+#undef SSS_KW
 }
 
 void launch_walk_plain(const WalkConst& c, const WalkSched& s, const TallyOut& t, uint32_t inst,

@@ -85,7 +85,7 @@ void launch_unit_prefix(const uint32_t* n_paths, uint32_t n, uint32_t C,
 void launch_walk_persistent(bool adj, int grid, int block, size_t smem, const WalkConst& c,
                             const WalkSched& s, const TallyOut& t, const GradIn& gi,
                             cudaStream_t st);
-const void* persistent_kernel_ptr(bool adj, bool layered, int hero, bool semi);
+const void* persistent_kernel_ptr(bool adj, bool layered, int hero, bool semi, int mode);
 void launch_walk_plain(const WalkConst& c, const WalkSched& s, const TallyOut& t, uint32_t inst,
                        uint32_t N, cudaStream_t st);
 void launch_finalize_tallies(const WalkConst& c, const WalkSched& s, const TallyOut& t,
